@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the all-pairs N-body step on GB300 (one JSON line on stdout).
+
+Workload (default): single large system, N = 262144 Plummer sphere (seed 1),
+G = 1, eps = 0.05, dt = 1e-3, FP32. One bench step = one step of the paper's
+update through the library (pack + force sum + half kick + drift). Metric:
+body-pair interactions per second, N^2 per step (self pairs counted, as the
+paper's 20 N^2 I / t GFLOPS convention does), and the fraction of the FP32
+FMA peak at 20 flops per interaction.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step on a bounded sample of the same workload (a subset of i-bodies against
+all N j-bodies).
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+single-system path has no exchange on one GPU); value sums the ranks'
+interactions over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Body-pair interactions/s and % of FP32 peak; adjoint-to-forward time ratio"
+UNIT = "interactions/s"
+FLOPS_PER_INTERACTION = 20  # the paper's convention (Section 4.1)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=262144)
+    ap.add_argument("--no-extras", action="store_true", help="skip the C3/C4/C5 side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def cpu_baseline(n_all, x, m, G, eps, seconds=10.0):
+    """The FP64 oracle as it stands, on every host core, over i-subsets of the
+    same system until `seconds` of work are done."""
+    import numpy as np
+
+    import oracle
+
+    chunk = 512
+    done_i = 0
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < seconds:
+        idx = np.arange(k * chunk, (k + 1) * chunk) % n_all
+        oracle.accel(x, m, G, eps, idx)
+        done_i += chunk
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": done_i * n_all / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 force sum of {done_i} i-bodies (chunks of {chunk}) against all {n_all} bodies "
+                      f"of the same system, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2203_08263_gb300 import ics
+
+    oracle.build()
+    n, G, eps = args.n, 1.0, 0.05
+    s = ics.plummer(n, seed=1)
+    sample = 2048
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = (np.arange(sample) * 127 + k * sample) % n
+        t0 = time.perf_counter()
+        oracle.accel(s.x, s.m, G, eps, idx)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample * n * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"single system N={n} Plummer (seed 1), eps=0.05, "
+                                                    f"one step; reference step = oracle force sum of {sample} "
+                                                    f"i-bodies x {n} j-bodies", "n": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{sample} i-bodies x {n} j-bodies per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def fp32_peak_tflops(props, sm_max_mhz):
+    # 128 FP32 lanes per SM, 2 flops per FMA, at the maximum SM clock
+    return props.multi_processor_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2203_08263_gb300 import build as nbuild
+    from paper_2203_08263_gb300 import ics
+    from paper_2203_08263_gb300.nbody import Context
+
+    nbuild.build()
+    n, G, eps, dt = args.n, 1.0, 0.05, 1e-3
+    s = ics.plummer(n, seed=1)
+    ctx = Context(G, eps, dt, device=local)
+    ctx.autotune(n)
+    cfg = ctx.get_config(n)
+    x = torch.tensor(s.x, dtype=torch.float32, device=dev)
+    v = torch.tensor(s.v, dtype=torch.float32, device=dev)
+    m = torch.tensor(s.m, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ctx.run(x, v, m, 1)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = ctx.launch_count
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between steps, outside the timed events
+        evs[k][0].record(stream)
+        ctx.run(x, v, m, 1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count - l0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    inter = float(n) * n
+    value = world * inter * args.steps / (tot_ms / 1e3)
+    ms_step = tot_ms / args.steps
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(props, sm_max)
+    achieved = FLOPS_PER_INTERACTION * inter / (ms_step / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                              "(max SM clock); 20 flops per interaction",
+                "kernel": "force_kernel<AccelF32x2> (+ its 1-launch pack, <0.1% of the step)"}
+
+    # end to end through the public C-ABI with host buffers: the call copies
+    # the state in, runs the step, copies it back and returns
+    xh = torch.tensor(s.x, dtype=torch.float32).pin_memory().numpy()
+    vh = torch.tensor(s.v, dtype=torch.float32).pin_memory().numpy()
+    mh = torch.tensor(s.m, dtype=torch.float32).pin_memory().numpy()
+    ctx.run(xh, vh, mh, 1)
+    ke = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.run(xh, vh, mh, 1)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * inter * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 7,
+           "d2h_bytes_per_step": n * 4 * 6, "steps": ke}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"single system N={n} Plummer (seed 1), G=1, eps=0.05, dt=1e-3, FP32; "
+                               "one bench step = one paper update (half kick + drift)",
+                   "n": n, "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "shape": cfg},
+        "roofline": roofline,
+        "interactions_per_s_per_gpu": inter * args.steps / (tot_ms / 1e3),
+        "gflops_20": FLOPS_PER_INTERACTION * value / 1e9,
+        "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["extras"] = extras(ctx, torch, dev, np)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n, s.x, s.m, G, eps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _timed(torch, dev, fn, reps=1):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / 1e3
+
+
+def extras(ctx0, torch, dev, np):
+    """Side measurements of the other rows: the precision form (C3), the
+    batched ensemble (C4) and the adjoint-to-forward ratio (C5)."""
+    import oracle
+    from paper_2203_08263_gb300 import ics
+    from paper_2203_08263_gb300.nbody import Context
+
+    out = {}
+    # C3: precision form, N = 2^20 Plummer (seed 2), FP64 state, 2 steps
+    n = 1 << 20
+    s = ics.plummer(n, seed=2)
+    c = Context(1.0, 0.05, 5e-4, precision="comp", device=dev.index)
+    f = torch.float64
+    x, v, m = (torch.tensor(a, dtype=f, device=dev) for a in (s.x, s.v, s.m))
+    a = c.accel(x, m)
+    idx = ics.subset_indices(n, 256, 2 + 1000)
+    err = np.linalg.norm(a.cpu().numpy()[idx] - oracle.accel(s.x, s.m, 1.0, 0.05, idx)) / \
+        np.linalg.norm(oracle.accel(s.x, s.m, 1.0, 0.05, idx))
+    c.run(x, v, m, 1)
+    t = _timed(torch, dev, lambda: c.run(x, v, m, 2))
+    out["c3_precision_form"] = {"n": n, "steps": 2, "interactions_per_s": 2 * float(n) * n / t,
+                                "accel_rel_l2_vs_fp64_oracle_256_subset": float(err), "s": t,
+                                "shape": c.get_config(n)}
+    c.close()
+    del x, v, m, a
+    # C4: batched ensemble, 512 systems, 100 steps, one persistent launch
+    off, bx, bv, bm = ics.ensemble(512, 3)
+    c = Context(1.0, 0.01, 1e-3, device=dev.index)
+    xb, vb, mb = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (bx, bv, bm))
+    offt = torch.tensor(off, dtype=torch.int64)
+    c.run_batched(offt, xb.clone(), vb.clone(), mb, 1)  # plan + capture
+    t = _timed(torch, dev, lambda: c.run_batched(offt, xb, vb, mb, 100))
+    sizes = np.diff(off).astype(np.float64)
+    out["c4_batched"] = {"systems": 512, "bodies": int(off[-1]), "steps": 100,
+                         "interactions_per_s": float((sizes ** 2).sum()) * 100 / t, "s": t}
+    c.close()
+    # C5: adjoint, N = 16384 cube (seed 4), T = 200, checkpoint every 20
+    n, T, k = 16384, 200, 20
+    s = ics.cube(n, seed=4, masses="equal")
+    xs = ics.targets(n, seed=4)
+    c = Context(1.0, 0.01, 1e-3, device=dev.index)
+    x0, v0, m = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (s.x, s.v, s.m))
+    ck = torch.empty((T // k + 1, n, 6), dtype=torch.float32, device=dev)
+    x, v = x0.clone(), v0.clone()
+    c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - torch.tensor(xs, dtype=torch.float32, device=dev))
+    vbT = torch.zeros_like(xbT)
+    c.adjoint(m, T, ck, k, xbT, vbT)
+
+    def fwd():
+        x.copy_(x0)
+        v.copy_(v0)
+        c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+
+    tf = _timed(torch, dev, fwd)
+    tb = _timed(torch, dev, lambda: c.adjoint(m, T, ck, k, xbT, vbT))
+    out["c5_adjoint"] = {"n": n, "T": T, "k": k, "forward_s": tf, "backward_s": tb, "ratio": tb / tf,
+                         "forward_interactions_per_s": float(n) * n * T / tf}
+    c.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

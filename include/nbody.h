@@ -1,0 +1,209 @@
+/*
+ * libnbody: all-pairs softened-gravity N-body on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the case study of Milla & Rucci, "Performance Comparison of
+ * Python Translators for a Multi-threaded CPU-bound Application"
+ * (arXiv 2203.08263):
+ *
+ *   force (Section 2.3; the j-loops of the Section 3.2.4 and 3.3.5 figures)
+ *     a_i = G * sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2),
+ *     summed over every j including j = i (which contributes exactly 0);
+ *   update (the Section 3.1.2 figure, split in two loops as in 3.2.3/3.3.5)
+ *     all a_i from the positions at the start of the step; then
+ *     v_i <- v_i + a_i dt / 2;  x_i <- x_i + v_i dt  (with the new v_i),
+ *     positions moved only after every body has been kicked.
+ *
+ * The paper prints no values for G, eps (its SOFT = eps^2) or dt; they are
+ * parameters here. eps must be > 0.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are contiguous, row-major: positions and velocities [n][3],
+ *     masses [n]. Element type: float32 when precision == NB_FP32; float64
+ *     when precision == NB_FP32_COMP_FP64_STATE (forces are then computed in
+ *     FP32 with compensated accumulation; state, gradients and diagnostics
+ *     stay FP64).
+ *   - Array pointers are caller-owned device pointers (e.g. torch tensors on
+ *     the context's device). nb_accel, nb_step and nb_run also accept host
+ *     pointers (pageable or pinned); the library then copies in and out
+ *     through its own device buffers and the call returns only after the
+ *     results are back on the host. Every pointer must be 4-byte (float32)
+ *     or 8-byte (float64) aligned.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) unless stated. Argument errors return at once and
+ *     launch nothing. Errors raised inside a kernel (a bounded wait that gave
+ *     up) are recorded in the context and returned by nb_sync or by the next
+ *     call on the context.
+ *   - The context owns all scratch memory (packed bodies, split partials,
+ *     trajectory segments, CUDA graphs, tuning tables). It grows that memory
+ *     on demand with cudaMalloc, outside any stream capture.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - n == 0 is a valid no-op. No call aborts the process.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_ABI_VERSION 1
+
+typedef struct nb_ctx nb_ctx;
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_INVALID = 1,     /* bad argument: NULL, n < 0, eps <= 0, misaligned ... */
+    NB_ERR_CUDA = 2,        /* a CUDA runtime call failed; see nb_last_error */
+    NB_ERR_NOMEM = 3,       /* device or host allocation failed */
+    NB_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    NB_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+} nb_status;
+
+typedef enum {
+    NB_FP32 = 0,                 /* FP32 state, FP32 forces */
+    NB_FP32_COMP_FP64_STATE = 1  /* FP64 state; FP32 forces, compensated sums */
+} nb_precision;
+
+typedef enum {
+    NB_SCHEME_PAPER = 0,  /* the printed update: half kick, then drift */
+    NB_SCHEME_KDK = 1     /* velocity Verlet, named but not printed (3.2.3, 3.3.7) */
+} nb_scheme;
+
+typedef struct {
+    double G;    /* gravitational constant (GRAVITY in the paper's listings) */
+    double eps;  /* softening length; the listings add SOFT = eps^2 to r^2 */
+    double dt;   /* time step (DT) */
+    int precision;         /* nb_precision */
+    int scheme;            /* nb_scheme; used by nb_step / nb_run */
+    int tile_override[4];  /* {threads per CTA, bodies per thread, j-split,
+                              j-tile bodies}; 0 = chosen by the autotuner */
+} nb_params;
+
+/* Library version; equals NB_ABI_VERSION of the header it was built from. */
+int nb_abi_version(void);
+
+/* Create a context on CUDA device `device` (cudaSetDevice is called). *out
+ * receives the context, or NULL on failure. The params are copied. Returns
+ * NB_ERR_INVALID for eps <= 0, a non-finite G/eps/dt or an unknown
+ * precision/scheme. */
+nb_status nb_create(nb_ctx **out, int device, const nb_params *p);
+
+/* Wait for the context's work on every stream it used, release everything it
+ * owns. NULL is ignored. */
+void nb_destroy(nb_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+const char *nb_status_string(nb_status s);
+
+/* Last error message recorded on ctx ("" if none); valid until the next call. */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Replace G, eps and dt (precision and scheme are fixed at creation). */
+nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
+
+/*
+ * Accelerations only (Section 2.3 force sum):
+ *   a[i][c] = G sum_j m_j (x_j - x_i)_c / (|x_j - x_i|^2 + eps^2)^(3/2).
+ * x [n][3], m [n] in the state type; a [n][3] in the state type (float32 or
+ * float64). Inputs are read-only.
+ */
+nb_status nb_accel(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a,
+                   void *stream);
+
+/* One step of the update selected by params.scheme, in place on x and v. */
+nb_status nb_step(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, void *stream);
+
+/*
+ * `steps` steps in place on x, v, replayed from a CUDA graph that the context
+ * captures once per (n, buffers, steps, checkpoint layout) and caches.
+ * ckpt (nullable, device): [steps/ckpt_every + 1][n][6] in the state type;
+ * slot k receives (x, v) after k*ckpt_every steps (slot 0 = the input state).
+ * ckpt_every must divide steps when ckpt != NULL. The paper scheme only when
+ * checkpointing.
+ */
+nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
+                 void *ckpt, int ckpt_every, void *stream);
+
+/*
+ * An ensemble of nsys independent systems, each advanced `steps` paper steps,
+ * all in one persistent cooperative kernel launch (replayed from a cached CUDA
+ * graph). System s owns bodies [offsets[s], offsets[s+1]); offsets (int64,
+ * nsys+1 entries, offsets[0] = 0, non-decreasing) may be a host or a device
+ * pointer. Systems do not interact. Each system's size must be at most
+ * nb_batched_max_n(). FP32 precision only.
+ */
+nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
+                         const void *m, int steps, void *stream);
+
+/* Largest system size nb_run_batched accepts. */
+int64_t nb_batched_max_n(void);
+
+/*
+ * Reverse mode of nb_run with the paper scheme. Given the checkpoints written
+ * by nb_run(..., ckpt, ckpt_every) over `steps` steps and the cotangents of
+ * the final state (xbar_T, vbar_T: [n][3]), writes the gradients of the same
+ * scalar loss w.r.t. the initial positions (xbar0 [n][3]), velocities
+ * (vbar0 [n][3]) and masses (mbar [n]). Each segment of ckpt_every steps is
+ * recomputed from its checkpoint and swept backwards:
+ *   vbar' = vbar + dt xbar;  abar = dt/2 vbar';
+ *   xbar += VJP_x(abar; x_t);  mbar += VJP_m(abar; x_t);  vbar = vbar'
+ * with the all-pairs vector-Jacobian product
+ *   VJP_x(abar)_k = G sum_j K(d_kj) (m_k abar_j - m_j abar_k),
+ *   VJP_m(abar)_k = -G sum_j abar_j . d_kj / s_kj^(3/2),
+ *   d_kj = x_j - x_k, s = |d|^2 + eps^2, K(d) = s^(-3/2) I - 3 s^(-5/2) d d^T.
+ * All arrays device, in the state type. Inputs are read-only.
+ */
+nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const void *ckpt,
+                     int ckpt_every, const void *xbar_T, const void *vbar_T, void *xbar0,
+                     void *vbar0, void *mbar, void *stream);
+
+/* One vector-Jacobian product of the acceleration at positions x:
+ * xbar = VJP_x(abar), mbar = VJP_m(abar) (formulas as in nb_adjoint). */
+nb_status nb_vjp(nb_ctx *ctx, int64_t n, const void *x, const void *m, const void *abar,
+                 void *xbar, void *mbar, void *stream);
+
+/*
+ * Diagnostics (synchronous): out (host, 6 doubles) receives total momentum
+ * P = sum m v (out[0..2]), kinetic energy KE = 1/2 sum m |v|^2 (out[3]), the
+ * softened potential Phi = -G sum_{i<j} m_i m_j / sqrt(|x_j-x_i|^2 + eps^2)
+ * (out[4]) and H' = KE + Phi/2 (out[5]), the energy the paper's half-kick
+ * update conserves as dt -> 0. Pair terms in FP32, all sums in FP64.
+ */
+nb_status nb_energy(nb_ctx *ctx, int64_t n, const void *x, const void *v, const void *m,
+                    double *out, void *stream);
+
+/*
+ * Time the candidate kernel shapes for problems of size n in mode `mode`
+ * (0 = forward, 1 = adjoint VJP) and store the fastest in the context's
+ * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). Calls
+ * that find no entry for their size bucket use a built-in heuristic instead.
+ * Synchronous.
+ */
+nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode);
+
+/* The launch shape the context would use for (n, mode):
+ * out[0..4] = {threads per CTA, bodies per thread, j-split, j-tile bodies,
+ * 1 if the shape came from a tuning run}. */
+nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5);
+
+/* Wait for the context's work on `stream`, then report (and clear) any error
+ * recorded by a kernel: NB_ERR_TIMEOUT if a bounded wait gave up. */
+nb_status nb_sync(nb_ctx *ctx, void *stream);
+
+/* Number of kernel launches the context issued (graph replays count each
+ * kernel node once per replay). */
+int64_t nb_launch_count(const nb_ctx *ctx);
+
+/* Debug knobs. NB_DBG_WAIT_TIMEOUT_NS: give up a device-side wait after this
+ * many nanoseconds (default 2e9; 0 gives up at the first unsuccessful poll,
+ * which forces the timeout path for tests). */
+typedef enum { NB_DBG_WAIT_TIMEOUT_NS = 1 } nb_debug_key;
+nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

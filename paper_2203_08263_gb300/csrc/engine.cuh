@@ -1,0 +1,738 @@
+// All-pairs tile engine: one kernel template serves every pair sum of the
+// library (forces, compensated forces, potential, adjoint VJP).
+//
+// Work decomposition. Bodies are packed in a "pair layout" (two bodies per
+// 32-byte record for the force sums: {x0,x1,y0,y1}, {z0,z1,m0,m1}) and padded
+// with zero-mass bodies to a multiple of the j-tile, so every j-tile is full
+// and padding contributes exactly 0. CTA b handles i-block b / S and j-split
+// b % S. Each of its NT consumer threads owns R i-bodies in registers; a
+// dedicated producer warp streams the split's j-tiles into a ring of shared
+// memory slots with 1-D bulk async copies (cp.async.bulk, completion counted
+// on an mbarrier per slot), and the consumers release slots through a second
+// mbarrier per slot. Every wait is bounded by a timeout and records an error
+// bit instead of hanging.
+//
+// Split reduction. With S > 1 each CTA writes its partial sums, and the last
+// CTA of an i-block to finish (atomic ticket) adds the S partials in split
+// order 0..S-1, so the result does not depend on scheduling, then runs the
+// policy's epilogue (write a, or kick + drift + repack for the next step).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ptx.cuh"
+
+namespace nb {
+
+constexpr int kStages = 4;        // ring depth
+constexpr int kPadBodies = 256;   // packed arrays hold a multiple of this
+constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
+
+enum ErrBits : int {
+    kErrFullWait = 1,   // consumer gave up waiting for a tile
+    kErrEmptyWait = 2,  // producer gave up waiting for a free slot
+    kErrDrain = 4,      // producer gave up waiting for its own copies
+    kErrGang = 8,       // batched kernel: gang barrier gave up
+};
+
+// Epilogue operations (runtime switch; never inside the pair loop).
+enum EpiOp : int {
+    kEpiAccel = 0,       // write a
+    kEpiKickDrift = 1,   // paper: v += a dt/2; x += v dt
+    kEpiKick2Drift = 2,  // velocity Verlet interior step: two half kicks, drift
+    kEpiKick = 3,        // velocity Verlet closing half kick
+    kEpiValue = 4,       // write the policy's per-body value (potential)
+    kEpiVjp = 5,         // adjoint: accumulate xbar, mbar
+};
+
+struct ForceArgs {
+    const float4 *src;    // j-records, pair layout; tile t at src + t * f4_per_tile
+    int64_t n;            // real bodies
+    int64_t npad;         // padded bodies (multiple of jt)
+    int jt;               // j-tile bodies (even)
+    int ntiles;           // npad / jt
+    int split;            // S
+    int iblocks;          // ceil(n / (NT * R))
+    float eps2;
+    double G;
+    double dt;
+    float4 *part;         // [S][iblocks * NT * R * PART_F4]
+    unsigned *counters;   // [iblocks], zero between launches
+    int *err;
+    uint64_t timeout_ns;
+    int op;               // EpiOp
+    void *x;              // state positions [n][3]
+    void *v;              // state velocities [n][3]
+    void *out;            // kEpiAccel: a [n][3]; kEpiValue: [n] doubles
+    float4 *xm_next;      // repacked positions for the next step (pair layout)
+    void *ckpt;           // nullable: (x, v) [n][6] after this step
+    // adjoint extras
+    void *xbar;           // [n][3] accumulated
+    void *mbar;           // [n] accumulated
+    const void *abar64;   // [n][3] FP64 cotangent of a (precision form)
+    const void *mass;     // [n] state-type masses (adjoint epilogue)
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Scalar from the pair layout: record q = i >> 1, lane h = i & 1; within a
+// record component c of body h sits at float 2c + h.
+// Force records (2 float4 per pair): c = 0 x, 1 y, 2 z, 3 m.
+__device__ __forceinline__ float pair_get(const float4 *base, int64_t i, int c) {
+    const float *p = reinterpret_cast<const float *>(base + (i >> 1) * 2);
+    return p[2 * c + (int)(i & 1)];
+}
+// Adjoint records (4 float4 per pair): c = 0..3 as above, 4..6 abar.
+__device__ __forceinline__ float vrec_get(const float4 *base, int64_t i, int c) {
+    const float *p = reinterpret_cast<const float *>(base + (i >> 1) * 4);
+    return p[2 * c + (int)(i & 1)];
+}
+__device__ __forceinline__ void pair_put(float4 *base, int64_t i, float x, float y, float z,
+                                         float m) {
+    float *p = reinterpret_cast<float *>(base + (i >> 1) * 2);
+    const int h = (int)(i & 1);
+    p[0 + h] = x;
+    p[2 + h] = y;
+    p[4 + h] = z;
+    p[6 + h] = m;
+}
+
+// Knuth's two-sum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// ------------------------------------------------------- the tile kernel
+
+template <int NT, int R, class P>
+__global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+    uint64_t *empty = full + kStages;
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw + 128);
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int ib = blockIdx.x / args.split;
+    const int sp = blockIdx.x % args.split;
+    const int t0 = (int)((int64_t)sp * args.ntiles / args.split);
+    const int t1 = (int)((int64_t)(sp + 1) * args.ntiles / args.split);
+    const int nt = t1 - t0;
+    const int f4_per_tile = (args.jt >> 1) * P::REC_F4;
+    const uint32_t tile_bytes = (uint32_t)f4_per_tile * 16u;
+    const int64_t ibase = (int64_t)ib * NT * R;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NT / 32);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    typename P::T tot[R];
+    if (warp == NT / 32) {
+        // ---------------- producer warp: one lane issues the bulk copies
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < nt; ++k) {
+                const int slot = k % kStages;
+                if (k >= kStages) {
+                    if (!mbar_wait(&empty[slot], ((k / kStages) - 1) & 1, args.timeout_ns)) {
+                        atomicOr(args.err, kErrEmptyWait);
+                        break;
+                    }
+                }
+                mbar_arrive_expect_tx(&full[slot], tile_bytes);
+                bulk_g2s(ring + slot * f4_per_tile, args.src + (int64_t)(t0 + k) * f4_per_tile,
+                         tile_bytes, &full[slot]);
+                issued = k + 1;
+            }
+            // never leave while our own copies may still be landing
+            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k) {
+                if (!mbar_wait(&full[k % kStages], (k / kStages) & 1, kDrainTimeoutNs))
+                    atomicOr(args.err, kErrDrain);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- consumers
+        typename P::I ist[R];
+        typename P::C cst;
+        P::consts(args, cst);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = ibase + r * NT + tid;
+            P::load_i(args, i < args.npad ? i : 0, ist[r]);
+            P::zero_total(tot[r]);
+        }
+        const int jpairs = args.jt >> 1;
+        for (int k = 0; k < nt; ++k) {
+            const int slot = k % kStages;
+            if (!mbar_wait(&full[slot], (k / kStages) & 1, args.timeout_ns)) {
+                atomicOr(args.err, kErrFullWait);
+                break;
+            }
+            const float4 *tile = ring + slot * f4_per_tile;
+            if constexpr (P::PER_TILE) {
+                typename P::A acc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) P::zero_acc(acc[r]);
+#pragma unroll 2
+                for (int jp = 0; jp < jpairs; ++jp) {
+                    float4 rec[P::REC_F4];
+#pragma unroll
+                    for (int q = 0; q < P::REC_F4; ++q) rec[q] = tile[jp * P::REC_F4 + q];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) P::interact(rec, ist[r], acc[r], cst);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) P::tile_done(acc[r], tot[r]);
+            } else {
+#pragma unroll 2
+                for (int jp = 0; jp < jpairs; ++jp) {
+                    float4 rec[P::REC_F4];
+#pragma unroll
+                    for (int q = 0; q < P::REC_F4; ++q) rec[q] = tile[jp * P::REC_F4 + q];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) P::interact(rec, ist[r], tot[r], cst);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+    }
+
+    // ---------------- epilogue (all threads reach the barriers below)
+    const bool consumer = warp < NT / 32;
+    if (args.split == 1) {
+        if (consumer) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int64_t i = ibase + r * NT + tid;
+                if (i < args.n) {
+                    typename P::F f;
+                    P::from_total(f, tot[r]);
+                    P::finish(args, i, f);
+                }
+            }
+        }
+        return;
+    }
+    const int64_t ni_pad = (int64_t)args.iblocks * NT * R;
+    if (consumer) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = ibase + r * NT + tid;
+            P::to_part(tot[r], args.part + ((int64_t)sp * ni_pad + i) * P::PART_F4);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned prev = atomicAdd(&args.counters[ib], 1u);
+        s_last = (prev == (unsigned)(args.split - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (consumer) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = ibase + r * NT + tid;
+            if (i < args.n) {
+                typename P::F f;
+                P::zero_final(f);
+                for (int s = 0; s < args.split; ++s)
+                    P::add_part(f, args.part + ((int64_t)s * ni_pad + i) * P::PART_F4);
+                P::finish(args, i, f);
+            }
+        }
+    }
+    if (tid == 0) args.counters[ib] = 0u;
+}
+
+// ------------------------------------------------ shared force epilogues
+
+// FP32 state: paper step, Verlet steps or plain output.
+__device__ __forceinline__ void finish_fp32(const ForceArgs &args, int64_t i, float ax, float ay,
+                                            float az) {
+    if (args.op == kEpiAccel) {
+        float *a = reinterpret_cast<float *>(args.out) + 3 * i;
+        a[0] = ax;
+        a[1] = ay;
+        a[2] = az;
+        return;
+    }
+    float *x = reinterpret_cast<float *>(args.x) + 3 * i;
+    float *v = reinterpret_cast<float *>(args.v) + 3 * i;
+    const float dt = (float)args.dt;
+    float a3[3] = {ax, ay, az};
+    float xs[3], vs[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float vc = v[c];
+        // v <- v + a*dt/2 (the printed half kick), rounded step by step
+        vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(a3[c], dt), 0.5f));
+        if (args.op == kEpiKick2Drift) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(a3[c], dt), 0.5f));
+        vs[c] = vc;
+        float xc = x[c];
+        if (args.op != kEpiKick) xc = __fadd_rn(xc, __fmul_rn(vc, dt));  // dp = v*dt; x += dp
+        xs[c] = xc;
+        v[c] = vc;
+        x[c] = xc;
+    }
+    if (args.op != kEpiKick)
+        pair_put(args.xm_next, i, xs[0], xs[1], xs[2], pair_get(args.src, i, 3));
+    if (args.ckpt) {
+        float *ck = reinterpret_cast<float *>(args.ckpt) + 6 * i;
+        ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
+        ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
+    }
+}
+
+// FP64 state (precision form): the update runs in double.
+__device__ __forceinline__ void finish_fp64(const ForceArgs &args, int64_t i, double ax,
+                                            double ay, double az) {
+    if (args.op == kEpiAccel) {
+        double *a = reinterpret_cast<double *>(args.out) + 3 * i;
+        a[0] = ax;
+        a[1] = ay;
+        a[2] = az;
+        return;
+    }
+    double *x = reinterpret_cast<double *>(args.x) + 3 * i;
+    double *v = reinterpret_cast<double *>(args.v) + 3 * i;
+    const double dt = args.dt;
+    double a3[3] = {ax, ay, az};
+    double xs[3], vs[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double vc = v[c];
+        vc = __dadd_rn(vc, __dmul_rn(__dmul_rn(a3[c], dt), 0.5));
+        if (args.op == kEpiKick2Drift) vc = __dadd_rn(vc, __dmul_rn(__dmul_rn(a3[c], dt), 0.5));
+        vs[c] = vc;
+        double xc = x[c];
+        if (args.op != kEpiKick) xc = __dadd_rn(xc, __dmul_rn(vc, dt));
+        xs[c] = xc;
+        v[c] = vc;
+        x[c] = xc;
+    }
+    if (args.op != kEpiKick)
+        pair_put(args.xm_next, i, (float)xs[0], (float)xs[1], (float)xs[2],
+                 pair_get(args.src, i, 3));
+    if (args.ckpt) {
+        double *ck = reinterpret_cast<double *>(args.ckpt) + 6 * i;
+        ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
+        ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
+    }
+}
+
+// ------------------------------------------------------------ policies
+
+// Plain FP32 force sum on the packed f32x2 pipe: each thread's i-body is held
+// duplicated ({-x_i, -x_i}) and one record supplies two j-bodies, so one
+// instruction evaluates the pair (i, j0), (i, j1). 12 FP32 operations and
+// 1 MUFU rsqrt per interaction: 3 add (d), 3 fma (r^2 + eps^2), 3 mul
+// (m y^3), 3 fma (accumulate).
+struct AccelF32x2 {
+    static constexpr int REC_F4 = 2;
+    static constexpr int PART_F4 = 1;
+    static constexpr bool PER_TILE = false;
+    struct I { float2 nx, ny, nz; };
+    struct T { float2 x, y, z; };
+    using A = T;
+    struct F { float x, y, z; };
+    struct C { float2 eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.nx = dup(-pair_get(a.src, i, 0));
+        s.ny = dup(-pair_get(a.src, i, 1));
+        s.nz = dup(-pair_get(a.src, i, 2));
+    }
+    __device__ static void zero_total(T &t) { t.x = t.y = t.z = f2(0.f, 0.f); }
+    __device__ static void zero_acc(A &t) { zero_total(t); }
+    __device__ static void tile_done(A &, T &) {}
+    __device__ __forceinline__ static void interact(const float4 (&rec)[2], const I &s, T &t,
+                                                    const C &c) {
+        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
+        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
+        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        const float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        const float2 y2 = __fmul2_rn(y, y);
+        float2 w = __fmul2_rn(f2(rec[1].z, rec[1].w), y);
+        w = __fmul2_rn(w, y2);
+        t.x = __ffma2_rn(w, dx, t.x);
+        t.y = __ffma2_rn(w, dy, t.y);
+        t.z = __ffma2_rn(w, dz, t.z);
+    }
+    __device__ static void to_part(const T &t, float4 *dst) {
+        *dst = make_float4(t.x.x + t.x.y, t.y.x + t.y.y, t.z.x + t.z.y, 0.f);
+    }
+    __device__ static void zero_final(F &f) { f.x = f.y = f.z = 0.f; }
+    __device__ static void add_part(F &f, const float4 *src) {
+        float4 p = __ldcg(src);
+        f.x += p.x;
+        f.y += p.y;
+        f.z += p.z;
+    }
+    __device__ static void from_total(F &f, const T &t) {
+        f.x = t.x.x + t.x.y;
+        f.y = t.y.x + t.y.y;
+        f.z = t.z.x + t.z.y;
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
+        const float G = (float)a.G;
+        finish_fp32(a, i, G * f.x, G * f.y, G * f.z);
+    }
+};
+
+// Same sum with scalar FP32 instructions (one j-body at a time), kept as the
+// baseline shape the autotuner can compare against.
+struct AccelScalar {
+    static constexpr int REC_F4 = 2;
+    static constexpr int PART_F4 = 1;
+    static constexpr bool PER_TILE = false;
+    struct I { float nx, ny, nz; };
+    struct T { float x, y, z; };
+    using A = T;
+    using F = AccelF32x2::F;
+    struct C { float eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = a.eps2; }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.nx = -pair_get(a.src, i, 0);
+        s.ny = -pair_get(a.src, i, 1);
+        s.nz = -pair_get(a.src, i, 2);
+    }
+    __device__ static void zero_total(T &t) { t.x = t.y = t.z = 0.f; }
+    __device__ static void zero_acc(A &t) { zero_total(t); }
+    __device__ static void tile_done(A &, T &) {}
+    __device__ __forceinline__ static void one(float xj, float yj, float zj, float mj, const I &s,
+                                               T &t, float eps2) {
+        const float dx = xj + s.nx, dy = yj + s.ny, dz = zj + s.nz;
+        float q = fmaf(dx, dx, eps2);
+        q = fmaf(dy, dy, q);
+        q = fmaf(dz, dz, q);
+        const float y = rsqrtf(q);
+        const float w = (mj * y) * (y * y);
+        t.x = fmaf(w, dx, t.x);
+        t.y = fmaf(w, dy, t.y);
+        t.z = fmaf(w, dz, t.z);
+    }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[2], const I &s, T &t,
+                                                    const C &c) {
+        one(rec[0].x, rec[0].z, rec[1].x, rec[1].z, s, t, c.eps2);
+        one(rec[0].y, rec[0].w, rec[1].y, rec[1].w, s, t, c.eps2);
+    }
+    __device__ static void to_part(const T &t, float4 *dst) { *dst = make_float4(t.x, t.y, t.z, 0.f); }
+    __device__ static void zero_final(F &f) { f.x = f.y = f.z = 0.f; }
+    __device__ static void add_part(F &f, const float4 *src) { AccelF32x2::add_part(f, src); }
+    __device__ static void from_total(F &f, const T &t) {
+        f.x = t.x;
+        f.y = t.y;
+        f.z = t.z;
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
+        const float G = (float)a.G;
+        finish_fp32(a, i, G * f.x, G * f.y, G * f.z);
+    }
+};
+
+// Precision form: FP32 pair terms with one Newton-Raphson refinement of the
+// MUFU reciprocal square root (y <- y + y/2 (1 - s y^2)), plain FP32 sums
+// within a j-tile, and the per-tile sums folded into a (hi, lo) pair with
+// Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
+// update run in FP64.
+struct AccelComp {
+    static constexpr int REC_F4 = 2;
+    static constexpr int PART_F4 = 2;
+    static constexpr bool PER_TILE = true;
+    using I = AccelF32x2::I;
+    struct A { float2 x, y, z; };
+    struct T { float hx, hy, hz, lx, ly, lz; };
+    struct F { double x, y, z; };
+    struct C { float2 eps2, one, half; };
+    __device__ static void consts(const ForceArgs &a, C &c) {
+        c.eps2 = dup(a.eps2);
+        c.one = dup(1.f);
+        c.half = dup(0.5f);
+    }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { AccelF32x2::load_i(a, i, s); }
+    __device__ static void zero_total(T &t) { t.hx = t.hy = t.hz = t.lx = t.ly = t.lz = 0.f; }
+    __device__ static void zero_acc(A &t) { t.x = t.y = t.z = f2(0.f, 0.f); }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[2], const I &s, A &t,
+                                                    const C &c) {
+        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
+        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
+        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        // Newton step for q^(-1/2): residual 1 - q y^2, correction y/2 * residual
+        const float2 qy = __fmul2_rn(q, y);
+        const float2 res = __ffma2_rn(neg2(qy), y, c.one);
+        y = __ffma2_rn(__fmul2_rn(c.half, y), res, y);
+        const float2 y2 = __fmul2_rn(y, y);
+        float2 w = __fmul2_rn(f2(rec[1].z, rec[1].w), y);
+        w = __fmul2_rn(w, y2);
+        t.x = __ffma2_rn(w, dx, t.x);
+        t.y = __ffma2_rn(w, dy, t.y);
+        t.z = __ffma2_rn(w, dz, t.z);
+    }
+    __device__ static void tile_done(const A &a, T &t) {
+        float s, e;
+        two_sum(t.hx, a.x.x + a.x.y, s, e); t.hx = s; t.lx += e;
+        two_sum(t.hy, a.y.x + a.y.y, s, e); t.hy = s; t.ly += e;
+        two_sum(t.hz, a.z.x + a.z.y, s, e); t.hz = s; t.lz += e;
+    }
+    __device__ static void to_part(const T &t, float4 *dst) {
+        dst[0] = make_float4(t.hx, t.hy, t.hz, 0.f);
+        dst[1] = make_float4(t.lx, t.ly, t.lz, 0.f);
+    }
+    __device__ static void zero_final(F &f) { f.x = f.y = f.z = 0.0; }
+    __device__ static void add_part(F &f, const float4 *src) {
+        float4 h = __ldcg(src), l = __ldcg(src + 1);
+        f.x += (double)h.x + (double)l.x;
+        f.y += (double)h.y + (double)l.y;
+        f.z += (double)h.z + (double)l.z;
+    }
+    __device__ static void from_total(F &f, const T &t) {
+        f.x = (double)t.hx + (double)t.lx;
+        f.y = (double)t.hy + (double)t.ly;
+        f.z = (double)t.hz + (double)t.lz;
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
+        finish_fp64(a, i, a.G * f.x, a.G * f.y, a.G * f.z);
+    }
+};
+
+// Softened potential per body, phi_i = sum_j m_j / sqrt(|d|^2 + eps^2) with
+// FP32 pair terms, FP32 sums within a tile, FP64 sums across tiles. The
+// epilogue removes the j = i term (m_i / eps, evaluated with the same FP32
+// operations the loop used) and writes m_i * phi_i as a double.
+struct Potential {
+    static constexpr int REC_F4 = 2;
+    static constexpr int PART_F4 = 1;
+    static constexpr bool PER_TILE = true;
+    using I = AccelF32x2::I;
+    struct A { float2 p; };
+    struct T { double p; };
+    struct F { double p; };
+    struct C { float2 eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { AccelF32x2::load_i(a, i, s); }
+    __device__ static void zero_total(T &t) { t.p = 0.0; }
+    __device__ static void zero_acc(A &t) { t.p = f2(0.f, 0.f); }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[2], const I &s, A &t,
+                                                    const C &c) {
+        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
+        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
+        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        const float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        t.p = __ffma2_rn(f2(rec[1].z, rec[1].w), y, t.p);
+    }
+    __device__ static void tile_done(const A &a, T &t) { t.p += (double)a.p.x + (double)a.p.y; }
+    __device__ static void to_part(const T &t, float4 *dst) {
+        *reinterpret_cast<double2 *>(dst) = make_double2(t.p, 0.0);
+    }
+    __device__ static void zero_final(F &f) { f.p = 0.0; }
+    __device__ static void add_part(F &f, const float4 *src) {
+        f.p += __ldcg(reinterpret_cast<const double2 *>(src)).x;
+    }
+    __device__ static void from_total(F &f, const T &t) { f.p = t.p; }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
+        const float mi = pair_get(a.src, i, 3);
+        const float self = __fmul_rn(mi, rsqrtf(a.eps2));
+        reinterpret_cast<double *>(a.out)[i] = (double)mi * (f.p - (double)self);
+    }
+};
+
+// Adjoint vector-Jacobian product of the force sum. For the i-body k and
+// every j (d = x_j - x_k, s = |d|^2 + eps^2, f = s^-3/2, h = s^-5/2,
+// e = abar_j . d, g = abar_k . d):
+//   U += f abar_j,  V += f m_j,  W += h (m_k e - m_j g) d,  P += f e
+// and the epilogue forms
+//   xbar_k += G (m_k U - V abar_k - 3 W),   mbar_k += -G P,
+// which equals G sum_j K(d)(m_k abar_j - m_j abar_k) and
+// -G sum_j f abar_j . d with K(d) = f I - 3 h d d^T. 27 FP32 operations and
+// one MUFU rsqrt per pair.
+struct VjpF32x2 {
+    static constexpr int REC_F4 = 4;
+    static constexpr int PART_F4 = 2;
+    static constexpr bool PER_TILE = false;
+    struct I { float2 nx, ny, nz, ax, ay, az, m; };
+    struct T { float2 ux, uy, uz, v, wx, wy, wz, p; };
+    using A = T;
+    struct F { float ux, uy, uz, v, wx, wy, wz, p; };
+    struct C { float2 eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.nx = dup(-vrec_get(a.src, i, 0));
+        s.ny = dup(-vrec_get(a.src, i, 1));
+        s.nz = dup(-vrec_get(a.src, i, 2));
+        s.m = dup(vrec_get(a.src, i, 3));
+        s.ax = dup(vrec_get(a.src, i, 4));
+        s.ay = dup(vrec_get(a.src, i, 5));
+        s.az = dup(vrec_get(a.src, i, 6));
+    }
+    __device__ static void zero_total(T &t) {
+        t.ux = t.uy = t.uz = t.v = t.wx = t.wy = t.wz = t.p = f2(0.f, 0.f);
+    }
+    __device__ static void zero_acc(A &t) { zero_total(t); }
+    __device__ static void tile_done(A &, T &) {}
+    template <bool REFINE>
+    __device__ __forceinline__ static void pair(const float4 (&rec)[4], const I &s, T &t,
+                                                float2 eps2) {
+        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
+        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
+        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
+        const float2 mj = f2(rec[1].z, rec[1].w);
+        const float2 ajx = f2(rec[2].x, rec[2].y);
+        const float2 ajy = f2(rec[2].z, rec[2].w);
+        const float2 ajz = f2(rec[3].x, rec[3].y);
+        float2 q = __ffma2_rn(dx, dx, eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        if constexpr (REFINE) {
+            const float2 qy = __fmul2_rn(q, y);
+            const float2 res = __ffma2_rn(neg2(qy), y, dup(1.f));
+            y = __ffma2_rn(__fmul2_rn(dup(0.5f), y), res, y);
+        }
+        const float2 y2 = __fmul2_rn(y, y);
+        const float2 f = __fmul2_rn(y, y2);
+        const float2 h = __fmul2_rn(f, y2);
+        float2 e = __fmul2_rn(ajx, dx);
+        e = __ffma2_rn(ajy, dy, e);
+        e = __ffma2_rn(ajz, dz, e);
+        float2 g = __fmul2_rn(s.ax, dx);
+        g = __ffma2_rn(s.ay, dy, g);
+        g = __ffma2_rn(s.az, dz, g);
+        const float2 c = __ffma2_rn(neg2(mj), g, __fmul2_rn(s.m, e));
+        const float2 hc = __fmul2_rn(h, c);
+        t.wx = __ffma2_rn(hc, dx, t.wx);
+        t.wy = __ffma2_rn(hc, dy, t.wy);
+        t.wz = __ffma2_rn(hc, dz, t.wz);
+        t.ux = __ffma2_rn(f, ajx, t.ux);
+        t.uy = __ffma2_rn(f, ajy, t.uy);
+        t.uz = __ffma2_rn(f, ajz, t.uz);
+        t.v = __fadd2_rn(__fmul2_rn(f, mj), t.v);
+        t.p = __ffma2_rn(f, e, t.p);
+    }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, T &t,
+                                                    const C &c) {
+        pair<false>(rec, s, t, c.eps2);
+    }
+    __device__ static void to_part(const T &t, float4 *dst) {
+        dst[0] = make_float4(t.ux.x + t.ux.y, t.uy.x + t.uy.y, t.uz.x + t.uz.y, t.v.x + t.v.y);
+        dst[1] = make_float4(t.wx.x + t.wx.y, t.wy.x + t.wy.y, t.wz.x + t.wz.y, t.p.x + t.p.y);
+    }
+    __device__ static void zero_final(F &f) {
+        f.ux = f.uy = f.uz = f.v = f.wx = f.wy = f.wz = f.p = 0.f;
+    }
+    __device__ static void add_part(F &f, const float4 *src) {
+        const float4 a = __ldcg(src), b = __ldcg(src + 1);
+        f.ux += a.x; f.uy += a.y; f.uz += a.z; f.v += a.w;
+        f.wx += b.x; f.wy += b.y; f.wz += b.z; f.p += b.w;
+    }
+    __device__ static void from_total(F &f, const T &t) {
+        float4 tmp[2];
+        to_part(t, tmp);
+        zero_final(f);
+        f.ux = tmp[0].x; f.uy = tmp[0].y; f.uz = tmp[0].z; f.v = tmp[0].w;
+        f.wx = tmp[1].x; f.wy = tmp[1].y; f.wz = tmp[1].z; f.p = tmp[1].w;
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t k, const F &f) {
+        const float G = (float)a.G;
+        const float mk = vrec_get(a.src, k, 3);
+        const float ak[3] = {vrec_get(a.src, k, 4), vrec_get(a.src, k, 5), vrec_get(a.src, k, 6)};
+        const float u[3] = {f.ux, f.uy, f.uz}, w[3] = {f.wx, f.wy, f.wz};
+        float *xb = reinterpret_cast<float *>(a.xbar) + 3 * k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * u[c] - f.v * ak[c] - 3.f * w[c]);
+        reinterpret_cast<float *>(a.mbar)[k] += -G * f.p;
+    }
+};
+
+// Precision form of the VJP: Newton-refined rsqrt, FP32 sums within a tile,
+// two-sum (hi, lo) across tiles, FP64 epilogue with FP64 m_k and abar_k.
+struct VjpComp {
+    static constexpr int REC_F4 = 4;
+    static constexpr int PART_F4 = 4;
+    static constexpr bool PER_TILE = true;
+    using I = VjpF32x2::I;
+    using A = VjpF32x2::T;
+    struct T { float h[8], l[8]; };
+    struct F { double s[8]; };
+    using C = VjpF32x2::C;
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { VjpF32x2::load_i(a, i, s); }
+    __device__ static void zero_total(T &t) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t.h[k] = t.l[k] = 0.f;
+    }
+    __device__ static void zero_acc(A &t) { VjpF32x2::zero_total(t); }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, A &t,
+                                                    const C &c) {
+        VjpF32x2::pair<true>(rec, s, t, c.eps2);
+    }
+    __device__ static void tile_done(const A &a, T &t) {
+        const float v[8] = {a.ux.x + a.ux.y, a.uy.x + a.uy.y, a.uz.x + a.uz.y, a.v.x + a.v.y,
+                            a.wx.x + a.wx.y, a.wy.x + a.wy.y, a.wz.x + a.wz.y, a.p.x + a.p.y};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float s, e;
+            two_sum(t.h[k], v[k], s, e);
+            t.h[k] = s;
+            t.l[k] += e;
+        }
+    }
+    __device__ static void to_part(const T &t, float4 *dst) {
+        dst[0] = make_float4(t.h[0], t.h[1], t.h[2], t.h[3]);
+        dst[1] = make_float4(t.h[4], t.h[5], t.h[6], t.h[7]);
+        dst[2] = make_float4(t.l[0], t.l[1], t.l[2], t.l[3]);
+        dst[3] = make_float4(t.l[4], t.l[5], t.l[6], t.l[7]);
+    }
+    __device__ static void zero_final(F &f) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f.s[k] = 0.0;
+    }
+    __device__ static void add_part(F &f, const float4 *src) {
+        const float4 h0 = __ldcg(src), h1 = __ldcg(src + 1), l0 = __ldcg(src + 2),
+                     l1 = __ldcg(src + 3);
+        const float hh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        const float ll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f.s[k] += (double)hh[k] + (double)ll[k];
+    }
+    __device__ static void from_total(F &f, const T &t) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f.s[k] = (double)t.h[k] + (double)t.l[k];
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t k, const F &f) {
+        const double G = a.G;
+        const double mk = reinterpret_cast<const double *>(a.mass)[k];
+        const double *ak = reinterpret_cast<const double *>(a.abar64) + 3 * k;
+        double *xb = reinterpret_cast<double *>(a.xbar) + 3 * k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * f.s[c] - f.s[3] * ak[c] - 3.0 * f.s[4 + c]);
+        reinterpret_cast<double *>(a.mbar)[k] += -G * f.s[7];
+    }
+};
+
+}  // namespace nb

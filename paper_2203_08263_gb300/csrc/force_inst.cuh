@@ -1,0 +1,33 @@
+// Instantiation helpers: one translation unit per policy keeps the build
+// parallel. Each entry pairs a launcher with an occupancy query.
+#pragma once
+#include "kernels.h"
+
+namespace nb {
+
+template <class P, int NT, int R>
+cudaError_t launch_force_inst(int jt, const ForceArgs &a, cudaStream_t st) {
+    const size_t smem = force_smem_bytes(P::REC_F4, jt);
+    auto k = force_kernel<NT, R, P>;
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)((int64_t)a.iblocks * a.split), NT + 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class P, int NT, int R>
+int occ_force_inst(int jt) {
+    int b = 0;
+    const size_t smem = force_smem_bytes(P::REC_F4, jt);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, force_kernel<NT, R, P>, NT + 32, smem) !=
+        cudaSuccess)
+        return 0;
+    return b;
+}
+
+#define NB_ENTRY(P, NT, R) {NT, R, &launch_force_inst<P, NT, R>, &occ_force_inst<P, NT, R>}
+
+}  // namespace nb

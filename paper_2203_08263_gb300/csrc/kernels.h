@@ -1,0 +1,62 @@
+// Internal launcher interface between the C-ABI layer (api.cu) and the
+// kernel translation units. Host code only sees these declarations.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.cuh"
+
+namespace nb {
+
+// Pair-sum policies compiled into the library.
+enum Pol : int {
+    kPolF32x2 = 0,   // plain FP32 forces, packed f32x2 arithmetic
+    kPolScalar = 1,  // plain FP32 forces, scalar arithmetic
+    kPolComp = 2,    // compensated FP32 forces, FP64 state
+    kPolPot = 3,     // softened potential (diagnostics)
+    kPolVjp = 4,     // adjoint VJP, FP32 state
+    kPolVjpComp = 5, // adjoint VJP, compensated, FP64 state
+    kPolCount = 6
+};
+
+struct Shape {
+    int pol, nt, r, split, jt;
+};
+
+struct ForceEntry {
+    int nt, r;
+    cudaError_t (*launch)(int jt, const ForceArgs &a, cudaStream_t st);
+    int (*occupancy)(int jt);  // resident CTAs per SM
+};
+
+// Table of compiled (NT, R) instances of a policy.
+const ForceEntry *force_table(int pol, int *count);
+int pol_rec_f4(int pol);   // float4 per j-pair record
+int pol_part_f4(int pol);  // float4 per i-body split partial
+
+inline size_t force_smem_bytes(int rec_f4, int jt) {
+    return 128 + (size_t)kStages * (size_t)(jt / 2) * rec_f4 * 16;
+}
+
+// ---- O(n) helpers (kern_misc.cu)
+cudaError_t launch_pack_f32(int64_t n, int64_t npad, const float *x, const float *v,
+                            const float *m, float4 *xm, float *ckpt0, cudaStream_t st);
+cudaError_t launch_pack_f64(int64_t n, int64_t npad, const double *x, const double *v,
+                            const double *m, float4 *xm, double *ckpt0, cudaStream_t st);
+// synthetic bodies for tuning runs
+cudaError_t launch_fill_synthetic(int64_t n, int64_t npad, float4 *xm, int rec_f4,
+                                  cudaStream_t st);
+// KE, P from (v, m) and sum of per-body potential terms; out[0..4] =
+// {Px, Py, Pz, KE, sum_i vals[i]}. `scratch` holds blocks * 5 doubles.
+cudaError_t launch_energy_reduce(int64_t n, const void *v, const void *m, int f64,
+                                 const double *vals, double *scratch, int blocks, double *out,
+                                 cudaStream_t st);
+// adjoint: vbar' = vbar + dt xbar; abar = dt/2 vbar'; pack (x_t, m, abar) VJP
+// records; restore/capture state helpers
+cudaError_t launch_adj_prepare(int64_t n, int64_t npad, int f64, const float4 *xm_t,
+                               const void *m, void *vbar, const void *xbar, double dt,
+                               float4 *rec, double *abar64, cudaStream_t st);
+cudaError_t launch_copy_ckpt_state(int64_t n, int f64, const void *ckpt_slot, void *x, void *v,
+                                   cudaStream_t st);
+
+}  // namespace nb

@@ -1,0 +1,146 @@
+"""GPU parity of the adjoint path (nb_vjp, nb_adjoint, the autograd Function)
+against the FP64 oracle and central finite differences. Bar: the precision
+form within 1e-6 of the FP64 reference gradient and 1e-4 of finite
+differences at N=64, T=20; the plain FP32 error is reported."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_08263_gb300 import ics
+from gpu_util import ensure_built, rel_l2, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    ensure_built()
+    from paper_2203_08263_gb300 import nbody
+    return nbody
+
+
+def _t(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 5e-5), ("comp", 1e-6)])
+@pytest.mark.parametrize("n", [2, 31, 257, 2000])
+def test_vjp_matches_oracle(nbm, prec, tol, n):
+    G, eps = 1.0, 0.01
+    s = ics.cube(n, seed=60 + n)
+    ab = np.random.default_rng(n).normal(size=(n, 3))
+    dt_ = torch.float32 if prec == "fp32" else torch.float64
+    ctx = nbm.Context(G, eps, 1e-3, precision=prec)
+    xb, mb = ctx.vjp(_t(s.x, dt_), _t(s.m, dt_), _t(ab, dt_))
+    rx, rm = oracle.vjp(s.x, s.m, G, eps, ab)
+    ex, em = rel_l2(to_np(xb), rx), rel_l2(to_np(mb), rm)
+    print(f"vjp {prec} n={n}: xbar {ex:.2e}, mbar {em:.2e}")
+    assert ex <= tol and em <= tol
+
+
+def _problem(n=64, T=20, seed=4):
+    s = ics.cube(n, seed=seed, masses="equal")
+    xstar = ics.targets(n, seed=seed)
+    return s, xstar, 1.0, 0.01, 1e-3, T
+
+
+@pytest.mark.parametrize("k", [1, 5, 20])
+def test_adjoint_precision_form_vs_fp64_oracle(nbm, k):
+    s, xstar, G, eps, dt, T = _problem()
+    n = s.n
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - _t(xstar, f))
+    gx, gv, gm = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    rx, rv, rm = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    errs = [rel_l2(to_np(gx), rx), rel_l2(to_np(gv), rv), rel_l2(to_np(gm), rm)]
+    print("adjoint comp k=%d: %s" % (k, ["%.2e" % e for e in errs]))
+    assert max(errs) <= 1e-6
+
+
+def test_adjoint_vs_central_differences(nbm):
+    s, xstar, G, eps, dt, T = _problem()
+    n = s.n
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ck = torch.empty((T // 20 + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=20)
+    xbT = 2 * (x - _t(xstar, f))
+    gx, gv, gm = (to_np(g) for g in ctx.adjoint(m, T, ck, 20, xbT, torch.zeros_like(xbT)))
+
+    def loss(x0, v0, m0):
+        xT, _ = oracle.run(x0, v0, m0, G, eps, dt, T)
+        return float(((xT - xstar) ** 2).sum())
+
+    rng = np.random.default_rng(0)
+    for got, which in ((gx, "x"), (gv, "v"), (gm, "m")):
+        # central differences along 6 random directions, h = 1e-6 max(1, |theta|)
+        base = {"x": s.x, "v": s.v, "m": s.m}[which]
+        for _ in range(6):
+            d = rng.normal(size=base.shape)
+            h = 1e-6 * max(1.0, float(np.abs(base).max()))
+            args_p = {"x": s.x, "v": s.v, "m": s.m}
+            args_m = dict(args_p)
+            args_p[which] = base + h * d
+            args_m[which] = base - h * d
+            fd = (loss(args_p["x"], args_p["v"], args_p["m"]) - loss(args_m["x"], args_m["v"], args_m["m"])) / (2 * h)
+            ad = float((got * d).sum())
+            assert abs(ad - fd) <= 1e-4 * max(abs(fd), 1e-12), (which, ad, fd)
+
+
+def test_adjoint_fp32_reported(nbm):
+    s, xstar, G, eps, dt, T = _problem()
+    n = s.n
+    f = torch.float32
+    ctx = nbm.Context(G, eps, dt)
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ck = torch.empty((T // 20 + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=20)
+    xbT = 2 * (x - _t(xstar, f))
+    gx, gv, gm = ctx.adjoint(m, T, ck, 20, xbT, torch.zeros_like(xbT))
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    rx, rv, rm = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    errs = [rel_l2(to_np(gx), rx), rel_l2(to_np(gv), rv), rel_l2(to_np(gm), rm)]
+    print("adjoint fp32: %s" % ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-3
+
+
+def test_autograd_function_gradients(nbm):
+    from paper_2203_08263_gb300.autograd import trajectory
+    s, xstar, G, eps, dt, T = _problem(n=48, T=10, seed=8)
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    x0 = _t(s.x, f).requires_grad_()
+    v0 = _t(s.v, f).requires_grad_()
+    m = _t(s.m, f).requires_grad_()
+    xT, vT = trajectory(x0, v0, m, ctx, T, 5)
+    loss = ((xT - _t(xstar, f)) ** 2).sum() + (vT ** 2).sum()
+    loss.backward()
+    xr, vr = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    rx, rv, rm = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xr - xstar), 2 * vr)
+    for got, ref in ((x0.grad, rx), (v0.grad, rv), (m.grad, rm)):
+        assert rel_l2(to_np(got), ref) <= 1e-6
+
+
+def test_adjoint_midsize_fp32_and_comp(nbm):
+    n, T, k = 2048, 40, 20
+    s, xstar, G, eps, dt, _ = _problem(n=n, T=T, seed=14)
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    ref = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    for prec, f, tol in (("comp", torch.float64, 1e-6), ("fp32", torch.float32, 1e-3)):
+        ctx = nbm.Context(G, eps, dt, precision=prec)
+        x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+        ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+        ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+        xbT = 2 * (x - _t(xstar, f))
+        got = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+        errs = [rel_l2(to_np(g), r) for g, r in zip(got, ref)]
+        print(f"adjoint {prec} n={n}: " + " ".join(f"{e:.2e}" for e in errs))
+        assert max(errs) <= tol
