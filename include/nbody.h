@@ -31,8 +31,9 @@
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  *     default stream) unless stated. Argument errors return at once and
  *     launch nothing. Errors raised inside a kernel (a bounded wait that gave
- *     up) are recorded in the context and returned by nb_sync or by the next
- *     call on the context.
+ *     up) are recorded in the context and returned by nb_sync, and by the
+ *     calls that wait for their own results (host-pointer calls, nb_energy,
+ *     nb_autotune, nb_measure_peaks).
  *   - The context owns all scratch memory (packed bodies, split partials,
  *     trajectory segments, CUDA graphs, tuning tables). It grows that memory
  *     on demand with cudaMalloc, outside any stream capture.
@@ -197,10 +198,22 @@ nb_status nb_sync(nb_ctx *ctx, void *stream);
 int64_t nb_launch_count(const nb_ctx *ctx);
 
 /* Debug knobs. NB_DBG_WAIT_TIMEOUT_NS: give up a device-side wait after this
- * many nanoseconds (default 2e9; 0 gives up at the first unsuccessful poll,
- * which forces the timeout path for tests). */
-typedef enum { NB_DBG_WAIT_TIMEOUT_NS = 1 } nb_debug_key;
+ * many nanoseconds (default 2e9; 0 gives up at the first poll that returns
+ * without the phase complete). NB_DBG_STALL_PRODUCER (value 0/1): the
+ * pair-sum kernels issue no j-tile copies, so every tile wait of nb_accel,
+ * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out; with a short
+ * timeout this exercises the error path without hanging (results are then
+ * invalid and nb_sync returns NB_ERR_TIMEOUT). */
+typedef enum { NB_DBG_WAIT_TIMEOUT_NS = 1, NB_DBG_STALL_PRODUCER = 2 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
+
+/*
+ * Measurement of the roofline denominators on this device (synchronous):
+ * out[0] = FP32 TFLOP/s issued as scalar FFMA, out[1] = FP32 TFLOP/s issued
+ * as packed f32x2 FMA, out[2] = MUFU reciprocal square roots, Gop/s. Each is
+ * one launch of independent FMA (or rsqrt) chains on every SM.
+ */
+nb_status nb_measure_peaks(nb_ctx *ctx, double *out3);
 
 #ifdef __cplusplus
 }

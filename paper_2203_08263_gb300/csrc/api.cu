@@ -85,6 +85,7 @@ struct nb_ctx {
     std::map<std::string, GraphEntry> graphs;
     uint64_t stamp = 0;
     uint64_t timeout_ns = 2000000000ull;
+    int debug = 0;
     int64_t launches = 0;
     std::map<std::string, TuneEntry> tuned;
     std::string tune_path;
@@ -331,6 +332,7 @@ ForceArgs base_args(nb_ctx *ctx, const Plan &p, int64_t n, const float4 *src) {
     a.counters = reinterpret_cast<unsigned *>(ctx->counters.p);
     a.err = ctx->err_word;
     a.timeout_ns = ctx->timeout_ns;
+    a.debug = ctx->debug;
     return a;
 }
 
@@ -391,7 +393,7 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
     char key[512];
     snprintf(key, sizeof key, "run|%lld|%p|%p|%p|%d|%p|%d|%d.%d.%d.%d.%d|%llu|%d|%a|%a|%a",
              (long long)n, x, v, m, steps, ckpt, ckpt_every, s.pol, s.nt, s.r, s.split, s.jt,
-             (unsigned long long)ctx->timeout_ns, ctx->p.scheme, ctx->p.G, ctx->p.eps, ctx->p.dt);
+             (unsigned long long)ctx->timeout_ns * 4 + ctx->debug, ctx->p.scheme, ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
@@ -802,7 +804,7 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
     char key[512];
     snprintf(key, sizeof key, "adj|%lld|%p|%d|%p|%d|%p|%p|%p|%d.%d.%d.%d.%d|%d.%d.%d.%d.%d|%llu|%a|%a|%a",
              (long long)n, m, steps, ckpt, k, xbar0, vbar0, mbar, sf.pol, sf.nt, sf.r, sf.split,
-             sf.jt, sv.pol, sv.nt, sv.r, sv.split, sv.jt, (unsigned long long)ctx->timeout_ns,
+             sf.jt, sv.pol, sv.nt, sv.r, sv.split, sv.jt, (unsigned long long)ctx->timeout_ns * 4 + ctx->debug,
              ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
@@ -1038,6 +1040,15 @@ nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5) {
     return NB_OK;
 }
 
+nb_status nb_measure_peaks(nb_ctx *ctx, double *out3) {
+    if (!ctx || !out3) return NB_ERR_INVALID;
+    NB_CUDA(cudaSetDevice(ctx->device));
+    NB_TRY(ensure(ctx, ctx->tune[5], 256));
+    NB_CUDA(measure_peaks(ctx->num_sms * 8, (float *)ctx->tune[5].p, ctx->side, out3));
+    ctx->launches += 6;
+    return sync_and_check(ctx, ctx->side);
+}
+
 nb_status nb_sync(nb_ctx *ctx, void *stream) {
     if (!ctx) return NB_ERR_INVALID;
     NB_CUDA(cudaSetDevice(ctx->device));
@@ -1051,6 +1062,11 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
     if (key == NB_DBG_WAIT_TIMEOUT_NS) {
         if (value < 0) return fail(ctx, NB_ERR_INVALID, "timeout must be >= 0");
         ctx->timeout_ns = (uint64_t)value;
+        return NB_OK;
+    }
+    if (key == NB_DBG_STALL_PRODUCER) {
+        if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
+        ctx->debug = value ? (ctx->debug | kDbgStallProducer) : (ctx->debug & ~kDbgStallProducer);
         return NB_OK;
     }
     return fail(ctx, NB_ERR_INVALID, "unknown debug key %d", key);

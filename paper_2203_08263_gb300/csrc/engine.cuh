@@ -35,6 +35,10 @@ enum ErrBits : int {
     kErrGang = 8,       // batched kernel: gang barrier gave up
 };
 
+enum DebugBits : int {
+    kDbgStallProducer = 1,  // producer issues nothing: every consumer wait runs out
+};
+
 // Epilogue operations (runtime switch; never inside the pair loop).
 enum EpiOp : int {
     kEpiAccel = 0,       // write a
@@ -71,6 +75,7 @@ struct ForceArgs {
     void *mbar;           // [n] accumulated
     const void *abar64;   // [n][3] FP64 cotangent of a (precision form)
     const void *mass;     // [n] state-type masses (adjoint epilogue)
+    int debug;            // bit 0: the producer issues no copies (timeout tests)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -110,6 +115,32 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 
 // ------------------------------------------------------- the tile kernel
 
+// One j-tile against the thread's R i-bodies. MASK drops the j == i pair
+// (needed only where a pair term does not vanish at d = 0: the VJP).
+template <int NT, int R, class P, bool MASK, class ACC>
+__device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
+                                          const typename P::I (&ist)[R], ACC (&acc)[R],
+                                          const typename P::C &cst, int64_t jbase, int64_t ibase,
+                                          int tid) {
+#pragma unroll 2
+    for (int jp = 0; jp < jpairs; ++jp) {
+        float4 rec[P::REC_F4];
+#pragma unroll
+        for (int q = 0; q < P::REC_F4; ++q) rec[q] = tile[jp * P::REC_F4 + q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if constexpr (MASK) {
+                const int64_t k = ibase + r * NT + tid;
+                const int64_t j0 = jbase + 2 * jp;
+                const float2 keep = f2(j0 == k ? 0.f : 1.f, j0 + 1 == k ? 0.f : 1.f);
+                P::interact_masked(rec, ist[r], acc[r], cst, keep);
+            } else {
+                P::interact(rec, ist[r], acc[r], cst);
+            }
+        }
+    }
+}
+
 template <int NT, int R, class P>
 __global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -143,7 +174,7 @@ __global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args)
         // ---------------- producer warp: one lane issues the bulk copies
         if (lane == 0) {
             int issued = 0;
-            for (int k = 0; k < nt; ++k) {
+            for (int k = 0; k < ((args.debug & kDbgStallProducer) ? 0 : nt); ++k) {
                 const int slot = k % kStages;
                 if (k >= kStages) {
                     if (!mbar_wait(&empty[slot], ((k / kStages) - 1) & 1, args.timeout_ns)) {
@@ -182,28 +213,36 @@ __global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args)
                 break;
             }
             const float4 *tile = ring + slot * f4_per_tile;
+            bool masked = false;
+            (void)masked;
+            if constexpr (P::SELF_MASK) {
+                const int64_t jb = (int64_t)(t0 + k) * args.jt;
+                masked = jb < ibase + (int64_t)NT * R && ibase < jb + args.jt;
+            }
             if constexpr (P::PER_TILE) {
                 typename P::A acc[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) P::zero_acc(acc[r]);
-#pragma unroll 2
-                for (int jp = 0; jp < jpairs; ++jp) {
-                    float4 rec[P::REC_F4];
-#pragma unroll
-                    for (int q = 0; q < P::REC_F4; ++q) rec[q] = tile[jp * P::REC_F4 + q];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) P::interact(rec, ist[r], acc[r], cst);
+                if constexpr (P::SELF_MASK) {
+                    if (masked)
+                        tile_pass<NT, R, P, true>(tile, jpairs, ist, acc, cst,
+                                                  (int64_t)(t0 + k) * args.jt, ibase, tid);
+                    else
+                        tile_pass<NT, R, P, false>(tile, jpairs, ist, acc, cst, 0, 0, tid);
+                } else {
+                    tile_pass<NT, R, P, false>(tile, jpairs, ist, acc, cst, 0, 0, tid);
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) P::tile_done(acc[r], tot[r]);
             } else {
-#pragma unroll 2
-                for (int jp = 0; jp < jpairs; ++jp) {
-                    float4 rec[P::REC_F4];
-#pragma unroll
-                    for (int q = 0; q < P::REC_F4; ++q) rec[q] = tile[jp * P::REC_F4 + q];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) P::interact(rec, ist[r], tot[r], cst);
+                if constexpr (P::SELF_MASK) {
+                    if (masked)
+                        tile_pass<NT, R, P, true>(tile, jpairs, ist, tot, cst,
+                                                  (int64_t)(t0 + k) * args.jt, ibase, tid);
+                    else
+                        tile_pass<NT, R, P, false>(tile, jpairs, ist, tot, cst, 0, 0, tid);
+                } else {
+                    tile_pass<NT, R, P, false>(tile, jpairs, ist, tot, cst, 0, 0, tid);
                 }
             }
             __syncwarp();
@@ -344,6 +383,7 @@ __device__ __forceinline__ void finish_fp64(const ForceArgs &args, int64_t i, do
 // 1 MUFU rsqrt per interaction: 3 add (d), 3 fma (r^2 + eps^2), 3 mul
 // (m y^3), 3 fma (accumulate).
 struct AccelF32x2 {
+    static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
     static constexpr bool PER_TILE = false;
@@ -401,6 +441,7 @@ struct AccelF32x2 {
 // Same sum with scalar FP32 instructions (one j-body at a time), kept as the
 // baseline shape the autotuner can compare against.
 struct AccelScalar {
+    static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
     static constexpr bool PER_TILE = false;
@@ -455,6 +496,7 @@ struct AccelScalar {
 // Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
 // update run in FP64.
 struct AccelComp {
+    static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 2;
     static constexpr bool PER_TILE = true;
@@ -523,6 +565,7 @@ struct AccelComp {
 // epilogue removes the j = i term (m_i / eps, evaluated with the same FP32
 // operations the loop used) and writes m_i * phi_i as a double.
 struct Potential {
+    static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
     static constexpr bool PER_TILE = true;
@@ -572,6 +615,7 @@ struct Potential {
 // -G sum_j f abar_j . d with K(d) = f I - 3 h d d^T. 27 FP32 operations and
 // one MUFU rsqrt per pair.
 struct VjpF32x2 {
+    static constexpr bool SELF_MASK = true;
     static constexpr int REC_F4 = 4;
     static constexpr int PART_F4 = 2;
     static constexpr bool PER_TILE = false;
@@ -595,9 +639,11 @@ struct VjpF32x2 {
     }
     __device__ static void zero_acc(A &t) { zero_total(t); }
     __device__ static void tile_done(A &, T &) {}
-    template <bool REFINE>
+    // `keep` is {1, 1} except on the j == k pair, whose terms would cancel
+    // only in the epilogue (f = eps^-3 there); zeroing y removes it exactly.
+    template <bool REFINE, bool MASK>
     __device__ __forceinline__ static void pair(const float4 (&rec)[4], const I &s, T &t,
-                                                float2 eps2) {
+                                                float2 eps2, float2 keep) {
         const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
         const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
         const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
@@ -614,6 +660,7 @@ struct VjpF32x2 {
             const float2 res = __ffma2_rn(neg2(qy), y, dup(1.f));
             y = __ffma2_rn(__fmul2_rn(dup(0.5f), y), res, y);
         }
+        if constexpr (MASK) y = __fmul2_rn(y, keep);
         const float2 y2 = __fmul2_rn(y, y);
         const float2 f = __fmul2_rn(y, y2);
         const float2 h = __fmul2_rn(f, y2);
@@ -636,7 +683,11 @@ struct VjpF32x2 {
     }
     __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, T &t,
                                                     const C &c) {
-        pair<false>(rec, s, t, c.eps2);
+        pair<false, false>(rec, s, t, c.eps2, dup(1.f));
+    }
+    __device__ __forceinline__ static void interact_masked(const float4 (&rec)[4], const I &s,
+                                                           T &t, const C &c, float2 keep) {
+        pair<false, true>(rec, s, t, c.eps2, keep);
     }
     __device__ static void to_part(const T &t, float4 *dst) {
         dst[0] = make_float4(t.ux.x + t.ux.y, t.uy.x + t.uy.y, t.uz.x + t.uz.y, t.v.x + t.v.y);
@@ -672,6 +723,7 @@ struct VjpF32x2 {
 // Precision form of the VJP: Newton-refined rsqrt, FP32 sums within a tile,
 // two-sum (hi, lo) across tiles, FP64 epilogue with FP64 m_k and abar_k.
 struct VjpComp {
+    static constexpr bool SELF_MASK = true;
     static constexpr int REC_F4 = 4;
     static constexpr int PART_F4 = 4;
     static constexpr bool PER_TILE = true;
@@ -689,7 +741,11 @@ struct VjpComp {
     __device__ static void zero_acc(A &t) { VjpF32x2::zero_total(t); }
     __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, A &t,
                                                     const C &c) {
-        VjpF32x2::pair<true>(rec, s, t, c.eps2);
+        VjpF32x2::pair<true, false>(rec, s, t, c.eps2, dup(1.f));
+    }
+    __device__ __forceinline__ static void interact_masked(const float4 (&rec)[4], const I &s,
+                                                           A &t, const C &c, float2 keep) {
+        VjpF32x2::pair<true, true>(rec, s, t, c.eps2, keep);
     }
     __device__ static void tile_done(const A &a, T &t) {
         const float v[8] = {a.ux.x + a.ux.y, a.uy.x + a.uy.y, a.uz.x + a.uz.y, a.v.x + a.v.y,

@@ -59,4 +59,7 @@ cudaError_t launch_adj_prepare(int64_t n, int64_t npad, int f64, const float4 *x
 cudaError_t launch_copy_ckpt_state(int64_t n, int f64, const void *ckpt_slot, void *x, void *v,
                                    cudaStream_t st);
 
+// FP32 FFMA / f32x2 FMA TFLOP/s and MUFU rsqrt Gop/s micro-benchmarks
+cudaError_t measure_peaks(int blocks, float *sink, cudaStream_t st, double out[3]);
+
 }  // namespace nb

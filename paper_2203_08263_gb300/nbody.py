@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnbody.so")
 NB_OK, NB_ERR_INVALID, NB_ERR_CUDA, NB_ERR_NOMEM, NB_ERR_TIMEOUT, NB_ERR_UNSUPPORTED = range(6)
 NB_FP32, NB_FP32_COMP_FP64_STATE = 0, 1
 NB_SCHEME_PAPER, NB_SCHEME_KDK = 0, 1
-NB_DBG_WAIT_TIMEOUT_NS = 1
+NB_DBG_WAIT_TIMEOUT_NS, NB_DBG_STALL_PRODUCER = 1, 2
 MODE_FORWARD, MODE_ADJOINT, MODE_POTENTIAL = 0, 1, 2
 
 # Every symbol include/nbody.h declares, with (restype, argtypes).
@@ -53,6 +53,7 @@ SIGNATURES = {
     "nb_sync": (_i, [_vp, _vp]),
     "nb_launch_count": (_i64, [_vp]),
     "nb_debug_set": (_i, [_vp, _i, _i64]),
+    "nb_measure_peaks": (_i, [_vp, _c.POINTER(_d)]),
 }
 
 _lock = threading.Lock()
@@ -231,6 +232,11 @@ class Context:
     @property
     def launch_count(self) -> int:
         return int(self.lib.nb_launch_count(self.h))
+
+    def measure_peaks(self) -> dict:
+        out = (_d * 3)()
+        self._check(self.lib.nb_measure_peaks(self.h, out), "nb_measure_peaks")
+        return {"ffma_tflops": out[0], "ffma2_tflops": out[1], "mufu_rsqrt_gops": out[2]}
 
     def debug_set(self, key: int, value: int):
         self._check(self.lib.nb_debug_set(self.h, int(key), int(value)), "nb_debug_set")

@@ -1,0 +1,75 @@
+"""Run one pair-sum kernel on a fixed launch shape, for timing and profiling.
+
+    python -m paper_2203_08263_gb300.profile_case --n 65536 --shape 128,4,16,256 --pol fp32
+    python -m paper_2203_08263_gb300.profile_case --peaks
+
+Input: Plummer sphere (seed 1), eps = 0.05. Prints the CUDA-event time per
+launch and the rate at 20 flops per interaction. --peaks runs the FFMA,
+f32x2-FMA and MUFU micro-benchmarks instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--shape", default="0,0,0,0", help="threads,bodies_per_thread,split,jtile (0 = auto)")
+    ap.add_argument("--pol", default="fp32", choices=["fp32", "comp", "vjp", "vjp-comp", "energy"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--peaks", action="store_true")
+    a = ap.parse_args()
+
+    import torch
+
+    from paper_2203_08263_gb300 import build, ics
+    from paper_2203_08263_gb300.nbody import MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, Context
+
+    build.build()
+    if a.peaks:
+        ctx = Context(1.0, 0.05, 1e-3)
+        runs = [ctx.measure_peaks() for _ in range(3)]
+        print(json.dumps({"runs": runs, "best": {k: max(r[k] for r in runs) for k in runs[0]}}))
+        return
+    shape = tuple(int(v) for v in a.shape.split(","))
+    prec = "comp" if a.pol in ("comp", "vjp-comp") else "fp32"
+    f = torch.float64 if prec == "comp" else torch.float32
+    dev = torch.device("cuda:0")
+    s = ics.plummer(a.n, seed=1)
+    ctx = Context(1.0, 0.05, 1e-3, precision=prec, tile_override=shape)
+    x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
+    ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
+    mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,
+            "energy": MODE_POTENTIAL}[a.pol]
+
+    def call():
+        if a.pol in ("fp32", "comp"):
+            ctx.accel(x, m)
+        elif a.pol in ("vjp", "vjp-comp"):
+            ctx.vjp(x, m, ab)
+        else:
+            ctx.energy(x, v, m)
+
+    call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ctx.sync()
+    t = min(times)
+    inter = float(a.n) ** 2
+    print(json.dumps({"n": a.n, "pol": a.pol, "shape": ctx.get_config(a.n, mode), "s": t, "times": times,
+                      "interactions_per_s": inter / t, "tflops_20": 20 * inter / t / 1e12}))
+
+
+if __name__ == "__main__":
+    main()
