@@ -18,6 +18,8 @@ LIB = os.path.join(OUT, "libnbody.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# extra nvcc flags (e.g. -DNB_JP_UNROLL=4); a change of flags rebuilds everything
+EXTRA = os.environ.get("NB_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -39,6 +41,10 @@ def _headers_mtime() -> float:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
+    stamp = os.path.join(OUT, "flags.txt")
+    flags_now = " ".join(ARCH + FLAGS + EXTRA)
+    if not os.path.exists(stamp) or open(stamp).read() != flags_now:
+        force = True
     hm = _headers_mtime()
     cc = nvcc()
     jobs = []
@@ -47,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(OUT, "obj", os.path.basename(src) + ".o")
         objs.append(obj)
         if (force or not os.path.exists(obj) or os.path.getmtime(obj) < max(hm, os.path.getmtime(src))):
-            jobs.append([cc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([cc, *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
@@ -64,6 +70,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags_now)
     return LIB
 
 

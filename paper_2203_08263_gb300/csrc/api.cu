@@ -37,7 +37,7 @@ const ForceEntry *force_table(int pol, int *count) {
         default: *count = 0; return nullptr;
     }
 }
-int pol_rec_f4(int pol) { return (pol == kPolVjp || pol == kPolVjpComp) ? 4 : 2; }
+int pol_rec_f4(int pol) { return pol == kPolVjp ? 4 : (pol == kPolVjpComp ? 5 : 2); }
 int pol_part_f4(int pol) {
     switch (pol) {
         case kPolComp: return 2;
@@ -80,7 +80,7 @@ struct nb_ctx {
     cudaStream_t side = nullptr;
     int *err_word = nullptr;
     // scratch
-    DevBuf xm[2], rec, part, counters, vals, red, traj, st_x, st_v, abar64, stage[4], tune[6];
+    DevBuf xm[2], rec, part, counters, vals, red, traj, traj64, st_x, st_v, abar64, stage[4], tune[6];
     DevBuf bat;  // batched-kernel scratch
     std::map<std::string, GraphEntry> graphs;
     uint64_t stamp = 0;
@@ -177,7 +177,9 @@ size_t esize(const nb_ctx *ctx) { return f64_state(ctx) ? 8 : 4; }
 nb_status validate_params(nb_ctx *ctx, double G, double eps, double dt) {
     if (!std::isfinite(G) || !std::isfinite(eps) || !std::isfinite(dt))
         return fail(ctx, NB_ERR_INVALID, "G, eps and dt must be finite");
-    if (!(eps > 0.0)) return fail(ctx, NB_ERR_INVALID, "eps must be > 0 (the j = i term is 0/0 otherwise)");
+    if (!(eps > 0.0) || !((float)(eps * eps) >= 1.17549435e-38f))
+        return fail(ctx, NB_ERR_INVALID,
+                    "eps must be > 0 with eps^2 a normal FP32 number (the j = i term is 0/0 otherwise)");
     return NB_OK;
 }
 
@@ -545,7 +547,8 @@ nb_status nb_create(nb_ctx **out, int device, const nb_params *p) {
     if (!out) return NB_ERR_INVALID;
     *out = nullptr;
     if (!p) return NB_ERR_INVALID;
-    if (!std::isfinite(p->G) || !std::isfinite(p->eps) || !std::isfinite(p->dt) || !(p->eps > 0))
+    if (!std::isfinite(p->G) || !std::isfinite(p->eps) || !std::isfinite(p->dt) || !(p->eps > 0) ||
+        !((float)(p->eps * p->eps) >= 1.17549435e-38f))
         return NB_ERR_INVALID;
     if (p->precision != NB_FP32 && p->precision != NB_FP32_COMP_FP64_STATE) return NB_ERR_INVALID;
     if (p->scheme != NB_SCHEME_PAPER && p->scheme != NB_SCHEME_KDK) return NB_ERR_INVALID;
@@ -584,7 +587,7 @@ void nb_destroy(nb_ctx *ctx) {
     cudaDeviceSynchronize();
     clear_graphs(ctx);
     DevBuf *bufs[] = {&ctx->xm[0], &ctx->xm[1], &ctx->rec,      &ctx->part,     &ctx->counters,
-                      &ctx->vals,  &ctx->red,   &ctx->traj,     &ctx->st_x,     &ctx->st_v,
+                      &ctx->vals,  &ctx->red,   &ctx->traj,  &ctx->traj64,   &ctx->st_x,     &ctx->st_v,
                       &ctx->abar64, &ctx->stage[0], &ctx->stage[1], &ctx->stage[2], &ctx->stage[3],
                       &ctx->tune[0], &ctx->tune[1], &ctx->tune[2], &ctx->tune[3], &ctx->tune[4],
                       &ctx->tune[5], &ctx->bat};
@@ -735,17 +738,18 @@ nb_status nb_vjp(nb_ctx *ctx, int64_t n, const void *x, const void *m, const voi
     NB_TRY(make_plan(ctx, s, n, &p));
     NB_TRY(plan_scratch(ctx, p));
     NB_TRY(ensure(ctx, ctx->xm[0], (size_t)p.npad * 16));
-    NB_TRY(ensure(ctx, ctx->rec, (size_t)p.npad * 32));
+    NB_TRY(ensure(ctx, ctx->rec, (size_t)p.npad * 8 * pol_rec_f4(s.pol)));
     NB_TRY(ensure(ctx, ctx->abar64, (size_t)n * 24));
     NB_TRY(ensure(ctx, ctx->st_v, (size_t)n * 3 * es));
     float4 *xm = (float4 *)ctx->xm[0].p;
-    NB_TRY(pack(ctx, n, p.npad, x, nullptr, m, xm, nullptr, st));
+    if (!f64_state(ctx)) NB_TRY(pack(ctx, n, p.npad, x, nullptr, m, xm, nullptr, st));
     // abar enters as vbar' with xbar = 0 and dt = 2: abar = dt/2 (vbar + dt*0)
     NB_CUDA(cudaMemcpyAsync(ctx->st_v.p, abar, (size_t)n * 3 * es, cudaMemcpyDeviceToDevice, st));
     NB_CUDA(cudaMemsetAsync(xbar, 0, (size_t)n * 3 * es, st));
     NB_CUDA(cudaMemsetAsync(mbar, 0, (size_t)n * es, st));
-    NB_CUDA(launch_adj_prepare(n, p.npad, f64_state(ctx) ? 1 : 0, xm, m, ctx->st_v.p, xbar, 2.0,
-                               (float4 *)ctx->rec.p, (double *)ctx->abar64.p, st));
+    NB_CUDA(launch_adj_prepare(n, p.npad, f64_state(ctx) ? 1 : 0, xm, (const double *)x, 3, m,
+                               ctx->st_v.p, xbar, 2.0, (float4 *)ctx->rec.p,
+                               (double *)ctx->abar64.p, st));
     ctx->launches += 1;
     ForceArgs a = base_args(ctx, p, n, (const float4 *)ctx->rec.p);
     a.op = kEpiVjp;
@@ -793,7 +797,9 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
     const int64_t npad = pf.npad;
     const int k = ckpt_every;
     NB_TRY(ensure(ctx, ctx->traj, (size_t)(k + 1) * npad * 16));
-    NB_TRY(ensure(ctx, ctx->rec, (size_t)npad * 32));
+    NB_TRY(ensure(ctx, ctx->rec, (size_t)npad * 8 * pol_rec_f4(sv.pol)));
+    const bool f64 = f64_state(ctx);
+    if (f64) NB_TRY(ensure(ctx, ctx->traj64, (size_t)k * n * 48));
     NB_TRY(ensure(ctx, ctx->st_x, b3));
     NB_TRY(ensure(ctx, ctx->st_v, b3));
     NB_TRY(ensure(ctx, ctx->abar64, (size_t)n * 24));
@@ -826,12 +832,17 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
                 a.x = ctx->st_x.p;
                 a.v = ctx->st_v.p;
                 a.xm_next = traj + (size_t)(t + 1) * (npad / 2) * 2;
+                // precision form: keep the FP64 positions of every step (slot t+1)
+                if (f64) a.ckpt = (char *)ctx->traj64.p + (size_t)(t + 1) * n * 48;
                 rs = launch_force(ctx, pf, a, ctx->side);
             }
             // 3) sweep the segment backwards
             for (int t = k - 1; rs == NB_OK && t >= 0; --t) {
                 const float4 *xm_t = traj + (size_t)t * (npad / 2) * 2;
-                ce = launch_adj_prepare(n, npad, f64_state(ctx) ? 1 : 0, xm_t, m, vbar0, xbar0,
+                const double *x64 = !f64 ? nullptr
+                                    : t == 0 ? (const double *)slot
+                                             : (const double *)((char *)ctx->traj64.p + (size_t)t * n * 48);
+                ce = launch_adj_prepare(n, npad, f64 ? 1 : 0, xm_t, x64, 6, m, vbar0, xbar0,
                                         ctx->p.dt, (float4 *)ctx->rec.p,
                                         (double *)ctx->abar64.p, ctx->side);
                 if (ce != cudaSuccess) { rs = fail(ctx, NB_ERR_CUDA, "%s", cudaGetErrorString(ce)); break; }
@@ -955,7 +966,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     }
     const int64_t npad = round_up(n, kPadBodies);
     const size_t es = esize(ctx);
-    NB_TRY(ensure(ctx, ctx->tune[0], (size_t)npad * 32));          // records
+    NB_TRY(ensure(ctx, ctx->tune[0], (size_t)npad * 40));          // records
     NB_TRY(ensure(ctx, ctx->tune[1], (size_t)n * 3 * 8, true));    // out / xbar
     NB_TRY(ensure(ctx, ctx->tune[2], (size_t)n * 8, true));        // mbar
     NB_TRY(ensure(ctx, ctx->tune[3], (size_t)n * 8, true));        // mass

@@ -24,6 +24,12 @@
 
 namespace nb {
 
+#ifndef NB_JP_UNROLL
+#define NB_JP_UNROLL 2  // j-pairs per unrolled step of the tile loop
+#endif
+#define NB_STR(x) #x
+#define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR(unroll n))
+
 constexpr int kStages = 4;        // ring depth
 constexpr int kPadBodies = 256;   // packed arrays hold a multiple of this
 constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
@@ -122,7 +128,7 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
                                           const typename P::I (&ist)[R], ACC (&acc)[R],
                                           const typename P::C &cst, int64_t jbase, int64_t ibase,
                                           int tid) {
-#pragma unroll 2
+    NB_PRAGMA_UNROLL(NB_JP_UNROLL)
     for (int jp = 0; jp < jpairs; ++jp) {
         float4 rec[P::REC_F4];
 #pragma unroll
@@ -409,7 +415,7 @@ struct AccelF32x2 {
         float2 q = __ffma2_rn(dx, dx, c.eps2);
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
-        const float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        const float2 y = rsqrt_mufu2(q);
         const float2 y2 = __fmul2_rn(y, y);
         float2 w = __fmul2_rn(f2(rec[1].z, rec[1].w), y);
         w = __fmul2_rn(w, y2);
@@ -465,7 +471,7 @@ struct AccelScalar {
         float q = fmaf(dx, dx, eps2);
         q = fmaf(dy, dy, q);
         q = fmaf(dz, dz, q);
-        const float y = rsqrtf(q);
+        const float y = rsqrt_mufu(q);
         const float w = (mj * y) * (y * y);
         t.x = fmaf(w, dx, t.x);
         t.y = fmaf(w, dy, t.y);
@@ -491,7 +497,7 @@ struct AccelScalar {
 };
 
 // Precision form: FP32 pair terms with one Newton-Raphson refinement of the
-// MUFU reciprocal square root (y <- y + y/2 (1 - s y^2)), plain FP32 sums
+// MUFU reciprocal square root (y <- y (3/2 - s y^2 / 2)), plain FP32 sums
 // within a j-tile, and the per-tile sums folded into a (hi, lo) pair with
 // Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
 // update run in FP64.
@@ -504,11 +510,11 @@ struct AccelComp {
     struct A { float2 x, y, z; };
     struct T { float hx, hy, hz, lx, ly, lz; };
     struct F { double x, y, z; };
-    struct C { float2 eps2, one, half; };
+    struct C { float2 eps2, mhalf, three_half; };
     __device__ static void consts(const ForceArgs &a, C &c) {
         c.eps2 = dup(a.eps2);
-        c.one = dup(1.f);
-        c.half = dup(0.5f);
+        c.mhalf = dup(-0.5f);
+        c.three_half = dup(1.5f);
     }
     __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { AccelF32x2::load_i(a, i, s); }
     __device__ static void zero_total(T &t) { t.hx = t.hy = t.hz = t.lx = t.ly = t.lz = 0.f; }
@@ -521,11 +527,10 @@ struct AccelComp {
         float2 q = __ffma2_rn(dx, dx, c.eps2);
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
-        float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
-        // Newton step for q^(-1/2): residual 1 - q y^2, correction y/2 * residual
-        const float2 qy = __fmul2_rn(q, y);
-        const float2 res = __ffma2_rn(neg2(qy), y, c.one);
-        y = __ffma2_rn(__fmul2_rn(c.half, y), res, y);
+        float2 y = rsqrt_mufu2(q);
+        // one Newton step for q^(-1/2): y <- y (3/2 - q y^2 / 2)
+        const float2 tq = __fmul2_rn(__fmul2_rn(q, c.mhalf), y);
+        y = __fmul2_rn(y, __ffma2_rn(tq, y, c.three_half));
         const float2 y2 = __fmul2_rn(y, y);
         float2 w = __fmul2_rn(f2(rec[1].z, rec[1].w), y);
         w = __fmul2_rn(w, y2);
@@ -586,7 +591,7 @@ struct Potential {
         float2 q = __ffma2_rn(dx, dx, c.eps2);
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
-        const float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
+        const float2 y = rsqrt_mufu2(q);
         t.p = __ffma2_rn(f2(rec[1].z, rec[1].w), y, t.p);
     }
     __device__ static void tile_done(const A &a, T &t) { t.p += (double)a.p.x + (double)a.p.y; }
@@ -600,7 +605,7 @@ struct Potential {
     __device__ static void from_total(F &f, const T &t) { f.p = t.p; }
     __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
         const float mi = pair_get(a.src, i, 3);
-        const float self = __fmul_rn(mi, rsqrtf(a.eps2));
+        const float self = __fmul_rn(mi, rsqrt_mufu(a.eps2));
         reinterpret_cast<double *>(a.out)[i] = (double)mi * (f.p - (double)self);
     }
 };
@@ -608,18 +613,22 @@ struct Potential {
 // Adjoint vector-Jacobian product of the force sum. For the i-body k and
 // every j (d = x_j - x_k, s = |d|^2 + eps^2, f = s^-3/2, h = s^-5/2,
 // e = abar_j . d, g = abar_k . d):
-//   U += f abar_j,  V += f m_j,  W += h (m_k e - m_j g) d,  P += f e
+//   U += f abar_j,  V += f m_j,  W += h (m_j g - m_k e) d,  P += f e
 // and the epilogue forms
-//   xbar_k += G (m_k U - V abar_k - 3 W),   mbar_k += -G P,
+//   xbar_k += G (m_k U - V abar_k + 3 W),   mbar_k += -G P,
 // which equals G sum_j K(d)(m_k abar_j - m_j abar_k) and
 // -G sum_j f abar_j . d with K(d) = f I - 3 h d d^T. 27 FP32 operations and
-// one MUFU rsqrt per pair.
+// one MUFU rsqrt per pair. The j == k pair is masked (its f = eps^-3 terms
+// would cancel only in the epilogue).
+//
+// Adjoint records, 4 float4 per pair of bodies:
+//   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,0,0}
 struct VjpF32x2 {
     static constexpr bool SELF_MASK = true;
     static constexpr int REC_F4 = 4;
     static constexpr int PART_F4 = 2;
     static constexpr bool PER_TILE = false;
-    struct I { float2 nx, ny, nz, ax, ay, az, m; };
+    struct I { float2 nx, ny, nz, ax, ay, az, nm; };  // nm = -m_k
     struct T { float2 ux, uy, uz, v, wx, wy, wz, p; };
     using A = T;
     struct F { float ux, uy, uz, v, wx, wy, wz, p; };
@@ -629,7 +638,7 @@ struct VjpF32x2 {
         s.nx = dup(-vrec_get(a.src, i, 0));
         s.ny = dup(-vrec_get(a.src, i, 1));
         s.nz = dup(-vrec_get(a.src, i, 2));
-        s.m = dup(vrec_get(a.src, i, 3));
+        s.nm = dup(-vrec_get(a.src, i, 3));
         s.ax = dup(vrec_get(a.src, i, 4));
         s.ay = dup(vrec_get(a.src, i, 5));
         s.az = dup(vrec_get(a.src, i, 6));
@@ -639,28 +648,10 @@ struct VjpF32x2 {
     }
     __device__ static void zero_acc(A &t) { zero_total(t); }
     __device__ static void tile_done(A &, T &) {}
-    // `keep` is {1, 1} except on the j == k pair, whose terms would cancel
-    // only in the epilogue (f = eps^-3 there); zeroing y removes it exactly.
-    template <bool REFINE, bool MASK>
-    __device__ __forceinline__ static void pair(const float4 (&rec)[4], const I &s, T &t,
-                                                float2 eps2, float2 keep) {
-        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
-        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
-        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
-        const float2 mj = f2(rec[1].z, rec[1].w);
-        const float2 ajx = f2(rec[2].x, rec[2].y);
-        const float2 ajy = f2(rec[2].z, rec[2].w);
-        const float2 ajz = f2(rec[3].x, rec[3].y);
-        float2 q = __ffma2_rn(dx, dx, eps2);
-        q = __ffma2_rn(dy, dy, q);
-        q = __ffma2_rn(dz, dz, q);
-        float2 y = f2(rsqrtf(q.x), rsqrtf(q.y));
-        if constexpr (REFINE) {
-            const float2 qy = __fmul2_rn(q, y);
-            const float2 res = __ffma2_rn(neg2(qy), y, dup(1.f));
-            y = __ffma2_rn(__fmul2_rn(dup(0.5f), y), res, y);
-        }
-        if constexpr (MASK) y = __fmul2_rn(y, keep);
+    // Pair terms from the separation (dx, dy, dz); y = s^-1/2 (already masked).
+    __device__ __forceinline__ static void terms(float2 dx, float2 dy, float2 dz, float2 y,
+                                                 float2 mj, float2 ajx, float2 ajy, float2 ajz,
+                                                 const I &s, T &t) {
         const float2 y2 = __fmul2_rn(y, y);
         const float2 f = __fmul2_rn(y, y2);
         const float2 h = __fmul2_rn(f, y2);
@@ -670,7 +661,7 @@ struct VjpF32x2 {
         float2 g = __fmul2_rn(s.ax, dx);
         g = __ffma2_rn(s.ay, dy, g);
         g = __ffma2_rn(s.az, dz, g);
-        const float2 c = __ffma2_rn(neg2(mj), g, __fmul2_rn(s.m, e));
+        const float2 c = __ffma2_rn(mj, g, __fmul2_rn(s.nm, e));  // m_j g - m_k e
         const float2 hc = __fmul2_rn(h, c);
         t.wx = __ffma2_rn(hc, dx, t.wx);
         t.wy = __ffma2_rn(hc, dy, t.wy);
@@ -678,16 +669,30 @@ struct VjpF32x2 {
         t.ux = __ffma2_rn(f, ajx, t.ux);
         t.uy = __ffma2_rn(f, ajy, t.uy);
         t.uz = __ffma2_rn(f, ajz, t.uz);
-        t.v = __fadd2_rn(__fmul2_rn(f, mj), t.v);
+        t.v = __ffma2_rn(f, mj, t.v);
         t.p = __ffma2_rn(f, e, t.p);
+    }
+    template <bool MASK>
+    __device__ __forceinline__ static void pair(const float4 (&rec)[4], const I &s, T &t,
+                                                float2 eps2, float2 keep) {
+        const float2 dx = __fadd2_rn(f2(rec[0].x, rec[0].y), s.nx);
+        const float2 dy = __fadd2_rn(f2(rec[0].z, rec[0].w), s.ny);
+        const float2 dz = __fadd2_rn(f2(rec[1].x, rec[1].y), s.nz);
+        float2 q = __ffma2_rn(dx, dx, eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        float2 y = rsqrt_mufu2(q);
+        if constexpr (MASK) y = __fmul2_rn(y, keep);
+        terms(dx, dy, dz, y, f2(rec[1].z, rec[1].w), f2(rec[2].x, rec[2].y),
+              f2(rec[2].z, rec[2].w), f2(rec[3].x, rec[3].y), s, t);
     }
     __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, T &t,
                                                     const C &c) {
-        pair<false, false>(rec, s, t, c.eps2, dup(1.f));
+        pair<false>(rec, s, t, c.eps2, dup(1.f));
     }
     __device__ __forceinline__ static void interact_masked(const float4 (&rec)[4], const I &s,
                                                            T &t, const C &c, float2 keep) {
-        pair<false, true>(rec, s, t, c.eps2, keep);
+        pair<true>(rec, s, t, c.eps2, keep);
     }
     __device__ static void to_part(const T &t, float4 *dst) {
         dst[0] = make_float4(t.ux.x + t.ux.y, t.uy.x + t.uy.y, t.uz.x + t.uz.y, t.v.x + t.v.y);
@@ -704,7 +709,6 @@ struct VjpF32x2 {
     __device__ static void from_total(F &f, const T &t) {
         float4 tmp[2];
         to_part(t, tmp);
-        zero_final(f);
         f.ux = tmp[0].x; f.uy = tmp[0].y; f.uz = tmp[0].z; f.v = tmp[0].w;
         f.wx = tmp[1].x; f.wy = tmp[1].y; f.wz = tmp[1].z; f.p = tmp[1].w;
     }
@@ -715,37 +719,83 @@ struct VjpF32x2 {
         const float u[3] = {f.ux, f.uy, f.uz}, w[3] = {f.wx, f.wy, f.wz};
         float *xb = reinterpret_cast<float *>(a.xbar) + 3 * k;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * u[c] - f.v * ak[c] - 3.f * w[c]);
+        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * u[c] - f.v * ak[c] + 3.f * w[c]);
         reinterpret_cast<float *>(a.mbar)[k] += -G * f.p;
     }
 };
 
-// Precision form of the VJP: Newton-refined rsqrt, FP32 sums within a tile,
-// two-sum (hi, lo) across tiles, FP64 epilogue with FP64 m_k and abar_k.
+// Precision form of the VJP. Positions enter as FP32 (hi, lo) pairs of the
+// FP64 state, and d = (x_j^hi - x_k^hi) + (x_j^lo - x_k^lo) keeps its
+// relative error at FP32 rounding even for close pairs (whose terms weigh
+// as |d|^-3); the rsqrt gets one Newton step; sums are FP32 within a tile
+// and two-summed (hi, lo) across tiles; the epilogue runs in FP64 with FP64
+// m_k and abar_k. Records, 5 float4 per pair of bodies:
+//   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,xl0,xl1} {yl0,yl1,zl0,zl1}
 struct VjpComp {
     static constexpr bool SELF_MASK = true;
-    static constexpr int REC_F4 = 4;
+    static constexpr int REC_F4 = 5;
     static constexpr int PART_F4 = 4;
     static constexpr bool PER_TILE = true;
-    using I = VjpF32x2::I;
+    struct I {
+        VjpF32x2::I b;
+        float2 nlx, nly, nlz;
+    };
     using A = VjpF32x2::T;
     struct T { float h[8], l[8]; };
     struct F { double s[8]; };
-    using C = VjpF32x2::C;
-    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
-    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { VjpF32x2::load_i(a, i, s); }
+    struct C { float2 eps2, mhalf, three_half; };
+    __device__ static void consts(const ForceArgs &a, C &c) {
+        c.eps2 = dup(a.eps2);
+        c.mhalf = dup(-0.5f);
+        c.three_half = dup(1.5f);
+    }
+    __device__ static float get(const float4 *base, int64_t i, int c) {
+        const float *p = reinterpret_cast<const float *>(base + (i >> 1) * 5);
+        return p[2 * c + (int)(i & 1)];
+    }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.b.nx = dup(-get(a.src, i, 0));
+        s.b.ny = dup(-get(a.src, i, 1));
+        s.b.nz = dup(-get(a.src, i, 2));
+        s.b.nm = dup(-get(a.src, i, 3));
+        s.b.ax = dup(get(a.src, i, 4));
+        s.b.ay = dup(get(a.src, i, 5));
+        s.b.az = dup(get(a.src, i, 6));
+        s.nlx = dup(-get(a.src, i, 7));
+        s.nly = dup(-get(a.src, i, 8));
+        s.nlz = dup(-get(a.src, i, 9));
+    }
     __device__ static void zero_total(T &t) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) t.h[k] = t.l[k] = 0.f;
     }
     __device__ static void zero_acc(A &t) { VjpF32x2::zero_total(t); }
-    __device__ __forceinline__ static void interact(const float4 (&rec)[4], const I &s, A &t,
-                                                    const C &c) {
-        VjpF32x2::pair<true, false>(rec, s, t, c.eps2, dup(1.f));
+    template <bool MASK>
+    __device__ __forceinline__ static void pair(const float4 (&rec)[5], const I &s, A &t,
+                                                const C &c, float2 keep) {
+        const float2 dx = __fadd2_rn(__fadd2_rn(f2(rec[0].x, rec[0].y), s.b.nx),
+                                     __fadd2_rn(f2(rec[3].z, rec[3].w), s.nlx));
+        const float2 dy = __fadd2_rn(__fadd2_rn(f2(rec[0].z, rec[0].w), s.b.ny),
+                                     __fadd2_rn(f2(rec[4].x, rec[4].y), s.nly));
+        const float2 dz = __fadd2_rn(__fadd2_rn(f2(rec[1].x, rec[1].y), s.b.nz),
+                                     __fadd2_rn(f2(rec[4].z, rec[4].w), s.nlz));
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        float2 y = rsqrt_mufu2(q);
+        const float2 tq = __fmul2_rn(__fmul2_rn(q, c.mhalf), y);
+        y = __fmul2_rn(y, __ffma2_rn(tq, y, c.three_half));
+        if constexpr (MASK) y = __fmul2_rn(y, keep);
+        VjpF32x2::terms(dx, dy, dz, y, f2(rec[1].z, rec[1].w), f2(rec[2].x, rec[2].y),
+                        f2(rec[2].z, rec[2].w), f2(rec[3].x, rec[3].y), s.b, t);
     }
-    __device__ __forceinline__ static void interact_masked(const float4 (&rec)[4], const I &s,
+    __device__ __forceinline__ static void interact(const float4 (&rec)[5], const I &s, A &t,
+                                                    const C &c) {
+        pair<false>(rec, s, t, c, dup(1.f));
+    }
+    __device__ __forceinline__ static void interact_masked(const float4 (&rec)[5], const I &s,
                                                            A &t, const C &c, float2 keep) {
-        VjpF32x2::pair<true, true>(rec, s, t, c.eps2, keep);
+        pair<true>(rec, s, t, c, keep);
     }
     __device__ static void tile_done(const A &a, T &t) {
         const float v[8] = {a.ux.x + a.ux.y, a.uy.x + a.uy.y, a.uz.x + a.uz.y, a.v.x + a.v.y,
@@ -786,7 +836,7 @@ struct VjpComp {
         const double *ak = reinterpret_cast<const double *>(a.abar64) + 3 * k;
         double *xb = reinterpret_cast<double *>(a.xbar) + 3 * k;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * f.s[c] - f.s[3] * ak[c] - 3.0 * f.s[4 + c]);
+        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * f.s[c] - f.s[3] * ak[c] + 3.0 * f.s[4 + c]);
         reinterpret_cast<double *>(a.mbar)[k] += -G * f.s[7];
     }
 };

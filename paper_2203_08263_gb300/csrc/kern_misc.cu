@@ -88,33 +88,70 @@ __global__ void energy_final_kernel(int blocks, const double *scratch, double *o
     }
 }
 
-template <class TS>
-__global__ void adj_prepare_kernel(int64_t n, int64_t npad, const float4 *__restrict__ xm_t,
-                                   const TS *__restrict__ m, TS *vbar, const TS *__restrict__ xbar,
-                                   double dt, float4 *rec, double *abar64) {
+// FP32 adjoint records from the packed positions x_t (4 float4 per pair).
+__global__ void adj_prepare_f32_kernel(int64_t n, int64_t npad, const float4 *__restrict__ xm_t,
+                                       const float *__restrict__ m, float *vbar,
+                                       const float *__restrict__ xbar, float dt, float4 *rec) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npad) return;
     float *p = reinterpret_cast<float *>(rec + (i >> 1) * 4);
     const int h = (int)(i & 1);
     if (i < n) {
-        const TS tdt = (TS)dt;
-        TS a[3];
+        float a[3];
         for (int c = 0; c < 3; ++c) {
-            TS vb = vbar[3 * i + c] + tdt * xbar[3 * i + c];  // vbar' = vbar + dt xbar
+            const float vb = vbar[3 * i + c] + dt * xbar[3 * i + c];  // vbar' = vbar + dt xbar
             vbar[3 * i + c] = vb;
-            a[c] = tdt / (TS)2 * vb;                           // abar = dt/2 vbar'
-            if (abar64) abar64[3 * i + c] = (double)a[c];
+            a[c] = dt / 2.0f * vb;                                     // abar = dt/2 vbar'
         }
         p[0 + h] = pair_get(xm_t, i, 0);
         p[2 + h] = pair_get(xm_t, i, 1);
         p[4 + h] = pair_get(xm_t, i, 2);
+        p[6 + h] = m[i];
+        p[8 + h] = a[0];
+        p[10 + h] = a[1];
+        p[12 + h] = a[2];
+        p[14 + h] = 0.f;
+    } else {
+        for (int k = 0; k < 8; ++k) p[2 * k + h] = 0.f;
+    }
+}
+
+// Precision-form adjoint records (5 float4 per pair): FP64 positions split
+// into FP32 hi + lo, FP32 abar, and the FP64 abar kept for the epilogue.
+__global__ void adj_prepare_f64_kernel(int64_t n, int64_t npad, const double *__restrict__ x64,
+                                       int x_stride, const double *__restrict__ m, double *vbar,
+                                       const double *__restrict__ xbar, double dt, float4 *rec,
+                                       double *abar64) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float *p = reinterpret_cast<float *>(rec + (i >> 1) * 5);
+    const int h = (int)(i & 1);
+    if (i < n) {
+        double a[3];
+        for (int c = 0; c < 3; ++c) {
+            const double vb = vbar[3 * i + c] + dt * xbar[3 * i + c];
+            vbar[3 * i + c] = vb;
+            a[c] = dt / 2.0 * vb;
+            abar64[3 * i + c] = a[c];
+        }
+        float hi[3], lo[3];
+        for (int c = 0; c < 3; ++c) {
+            const double xc = x64[(int64_t)x_stride * i + c];
+            hi[c] = (float)xc;
+            lo[c] = (float)(xc - (double)hi[c]);
+        }
+        p[0 + h] = hi[0];
+        p[2 + h] = hi[1];
+        p[4 + h] = hi[2];
         p[6 + h] = (float)m[i];
         p[8 + h] = (float)a[0];
         p[10 + h] = (float)a[1];
         p[12 + h] = (float)a[2];
-        p[14 + h] = 0.f;
+        p[14 + h] = lo[0];
+        p[16 + h] = lo[1];
+        p[18 + h] = lo[2];
     } else {
-        for (int k = 0; k < 8; ++k) p[2 * k + h] = 0.f;
+        for (int k = 0; k < 10; ++k) p[2 * k + h] = 0.f;
     }
 }
 
@@ -165,16 +202,16 @@ cudaError_t launch_energy_reduce(int64_t n, const void *v, const void *m, int f6
 }
 
 cudaError_t launch_adj_prepare(int64_t n, int64_t npad, int f64, const float4 *xm_t,
-                               const void *m, void *vbar, const void *xbar, double dt,
-                               float4 *rec, double *abar64, cudaStream_t st) {
+                               const double *x64, int x_stride, const void *m, void *vbar,
+                               const void *xbar, double dt, float4 *rec, double *abar64,
+                               cudaStream_t st) {
     if (f64)
-        adj_prepare_kernel<double><<<blocks_for(npad), kThreads, 0, st>>>(
-            n, npad, xm_t, (const double *)m, (double *)vbar, (const double *)xbar, dt, rec,
-            abar64);
+        adj_prepare_f64_kernel<<<blocks_for(npad), kThreads, 0, st>>>(
+            n, npad, x64, x_stride, (const double *)m, (double *)vbar, (const double *)xbar, dt,
+            rec, abar64);
     else
-        adj_prepare_kernel<float><<<blocks_for(npad), kThreads, 0, st>>>(
-            n, npad, xm_t, (const float *)m, (float *)vbar, (const float *)xbar, dt, rec,
-            abar64);
+        adj_prepare_f32_kernel<<<blocks_for(npad), kThreads, 0, st>>>(
+            n, npad, xm_t, (const float *)m, (float *)vbar, (const float *)xbar, (float)dt, rec);
     return cudaGetLastError();
 }
 

@@ -53,9 +53,12 @@ cudaError_t launch_energy_reduce(int64_t n, const void *v, const void *m, int f6
                                  cudaStream_t st);
 // adjoint: vbar' = vbar + dt xbar; abar = dt/2 vbar'; pack (x_t, m, abar) VJP
 // records; restore/capture state helpers
+// FP32: positions from the packed xm_t. FP64 (precision form): positions
+// from x64 (row stride x_stride doubles), split into hi/lo records.
 cudaError_t launch_adj_prepare(int64_t n, int64_t npad, int f64, const float4 *xm_t,
-                               const void *m, void *vbar, const void *xbar, double dt,
-                               float4 *rec, double *abar64, cudaStream_t st);
+                               const double *x64, int x_stride, const void *m, void *vbar,
+                               const void *xbar, double dt, float4 *rec, double *abar64,
+                               cudaStream_t st);
 cudaError_t launch_copy_ckpt_state(int64_t n, int f64, const void *ckpt_slot, void *x, void *v,
                                    cudaStream_t st);
 

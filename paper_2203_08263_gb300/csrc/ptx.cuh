@@ -73,4 +73,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// MUFU reciprocal square root without the denormal-input path (PTX
+// rsqrt.approx.ftz.f32). Every argument in this library is >= eps^2, a normal
+// float (the context rejects smaller eps).
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 rsqrt_mufu2(float2 x) {
+    return make_float2(rsqrt_mufu(x.x), rsqrt_mufu(x.y));
+}
+
 }  // namespace nb
