@@ -215,6 +215,31 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
  */
 nb_status nb_measure_peaks(nb_ctx *ctx, double *out3);
 
+/*
+ * nb_accel_noalloc: the FP32 force sum of nb_accel for callers that cannot
+ * allocate device memory when they need it: code running while a stream
+ * capture is active (cudaMalloc is refused in global capture mode), processes
+ * whose device memory is owned by a pooling allocator, and services whose
+ * footprint must be fixed when the library loads. The paper has no
+ * counterpart; this is a deployment variant of nb_accel.
+ *
+ * Needs no context and calls no allocator: its working memory (packed
+ * bodies, split partials, tickets) is a file-scope device array of about
+ * 4.6 MB, reserved on every GPU that loads the library until the process
+ * exits. n must be at most NB_NOALLOC_MAX_N (else NB_ERR_INVALID).
+ * x [n][3], m [n], a [n][3]: float32 device pointers on the current device;
+ * a = G sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2), asynchronous
+ * on `stream`. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and the SM count; make that first call
+ * before any stream capture. Every call shares the one array, so calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller. Device-side wait failures are
+ * not reported (the error word is cleared by the next call).
+ */
+#define NB_NOALLOC_MAX_N 32768
+nb_status nb_accel_noalloc(int64_t n, const float *x, const float *m, float *a, double G,
+                           double eps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

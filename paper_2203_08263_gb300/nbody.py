@@ -54,7 +54,9 @@ SIGNATURES = {
     "nb_launch_count": (_i64, [_vp]),
     "nb_debug_set": (_i, [_vp, _i, _i64]),
     "nb_measure_peaks": (_i, [_vp, _c.POINTER(_d)]),
+    "nb_accel_noalloc": (_i, [_i64, _vp, _vp, _vp, _d, _d, _vp]),
 }
+NB_NOALLOC_MAX_N = 32768
 
 _lock = threading.Lock()
 _lib = None
