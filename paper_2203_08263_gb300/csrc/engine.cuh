@@ -30,7 +30,12 @@ namespace nb {
 #define NB_STR(x) #x
 #define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR(unroll n))
 
+#ifndef NB_PRODUCER_WARP
+#define NB_PRODUCER_WARP 1  // 1: a dedicated warp issues the copies; 0: consumer thread 0 does
+#endif
+
 constexpr int kStages = 4;        // ring depth
+constexpr int kProducerThreads = NB_PRODUCER_WARP ? 32 : 0;
 constexpr int kPadBodies = 256;   // packed arrays hold a multiple of this
 constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
 
@@ -147,8 +152,15 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
     }
 }
 
+// Without the producer warp, ask for 512 resident threads per SM at R <= 4
+// (registers <= 128), which is what the extra warp used to cost.
+template <int NT, int R>
+constexpr int min_blocks() {
+    return (NB_PRODUCER_WARP || R > 4) ? 1 : 512 / NT;
+}
+
 template <int NT, int R, class P>
-__global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args) {
+__global__ void __launch_bounds__(NT + kProducerThreads, (min_blocks<NT, R>())) force_kernel(const ForceArgs args) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + kStages;
@@ -176,6 +188,7 @@ __global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args)
     __syncthreads();
 
     typename P::T tot[R];
+#if NB_PRODUCER_WARP
     if (warp == NT / 32) {
         // ---------------- producer warp: one lane issues the bulk copies
         if (lane == 0) {
@@ -255,6 +268,95 @@ __global__ void __launch_bounds__(NT + 32, 1) force_kernel(const ForceArgs args)
             if (lane == 0) mbar_arrive(&empty[slot]);
         }
     }
+
+#else
+    {
+        // consumer thread 0 also streams the tiles: the first kStages up
+        // front, then after tile k it refills the slot that tile k-1 used
+        // (one tile of slack for the other warps to release it).
+        int issued = 0;
+        bool stop = (args.debug & kDbgStallProducer) != 0;
+        if (tid == 0 && !stop) {
+            for (int k = 0; k < nt && k < kStages; ++k) {
+                mbar_arrive_expect_tx(&full[k], tile_bytes);
+                bulk_g2s(ring + k * f4_per_tile, args.src + (int64_t)(t0 + k) * f4_per_tile,
+                         tile_bytes, &full[k]);
+                issued = k + 1;
+            }
+        }
+        typename P::I ist[R];
+        typename P::C cst;
+        P::consts(args, cst);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = ibase + r * NT + tid;
+            P::load_i(args, i < args.npad ? i : 0, ist[r]);
+            P::zero_total(tot[r]);
+        }
+        const int jpairs = args.jt >> 1;
+        for (int k = 0; k < nt; ++k) {
+            const int slot = k % kStages;
+            if (!mbar_wait(&full[slot], (k / kStages) & 1, args.timeout_ns)) {
+                atomicOr(args.err, kErrFullWait);
+                break;
+            }
+            const float4 *tile = ring + slot * f4_per_tile;
+            bool masked = false;
+            (void)masked;
+            if constexpr (P::SELF_MASK) {
+                const int64_t jb = (int64_t)(t0 + k) * args.jt;
+                masked = jb < ibase + (int64_t)NT * R && ibase < jb + args.jt;
+            }
+            if constexpr (P::PER_TILE) {
+                typename P::A acc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) P::zero_acc(acc[r]);
+                if constexpr (P::SELF_MASK) {
+                    if (masked)
+                        tile_pass<NT, R, P, true>(tile, jpairs, ist, acc, cst,
+                                                  (int64_t)(t0 + k) * args.jt, ibase, tid);
+                    else
+                        tile_pass<NT, R, P, false>(tile, jpairs, ist, acc, cst, 0, 0, tid);
+                } else {
+                    tile_pass<NT, R, P, false>(tile, jpairs, ist, acc, cst, 0, 0, tid);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) P::tile_done(acc[r], tot[r]);
+            } else {
+                if constexpr (P::SELF_MASK) {
+                    if (masked)
+                        tile_pass<NT, R, P, true>(tile, jpairs, ist, tot, cst,
+                                                  (int64_t)(t0 + k) * args.jt, ibase, tid);
+                    else
+                        tile_pass<NT, R, P, false>(tile, jpairs, ist, tot, cst, 0, 0, tid);
+                } else {
+                    tile_pass<NT, R, P, false>(tile, jpairs, ist, tot, cst, 0, 0, tid);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (tid == 0 && !stop && k >= 1 && k - 1 + kStages < nt) {
+                const int kp = k - 1, kr = k - 1 + kStages, rs = kp % kStages;
+                if (!mbar_wait(&empty[rs], (kp / kStages) & 1, args.timeout_ns)) {
+                    atomicOr(args.err, kErrEmptyWait);
+                    stop = true;
+                } else {
+                    mbar_arrive_expect_tx(&full[rs], tile_bytes);
+                    bulk_g2s(ring + rs * f4_per_tile, args.src + (int64_t)(t0 + kr) * f4_per_tile,
+                             tile_bytes, &full[rs]);
+                    issued = kr + 1;
+                }
+            }
+        }
+        if (tid == 0) {
+            // never leave while our own copies may still be landing
+            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k) {
+                if (!mbar_wait(&full[k % kStages], (k / kStages) & 1, kDrainTimeoutNs))
+                    atomicOr(args.err, kErrDrain);
+            }
+        }
+    }
+#endif
 
     // ---------------- epilogue (all threads reach the barriers below)
     const bool consumer = warp < NT / 32;

@@ -14,7 +14,7 @@ cudaError_t launch_force_inst(int jt, const ForceArgs &a, cudaStream_t st) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)((int64_t)a.iblocks * a.split), NT + 32, smem, st>>>(a);
+    k<<<(unsigned)((int64_t)a.iblocks * a.split), NT + kProducerThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -22,7 +22,7 @@ template <class P, int NT, int R>
 int occ_force_inst(int jt) {
     int b = 0;
     const size_t smem = force_smem_bytes(P::REC_F4, jt);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, force_kernel<NT, R, P>, NT + 32, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, force_kernel<NT, R, P>, NT + kProducerThreads, smem) !=
         cudaSuccess)
         return 0;
     return b;
