@@ -82,6 +82,9 @@ struct nb_ctx {
     // scratch
     DevBuf xm[2], rec, part, counters, vals, red, traj, traj64, st_x, st_v, abar64, stage[4], tune[6];
     DevBuf bat;  // batched-kernel scratch
+    // adjoint: ping-pong segment buffers and the recompute stream's split scratch
+    DevBuf adj_traj[2], adj_traj64[2], adj_x[2], adj_v[2], part2, counters2;
+    cudaStream_t side2 = nullptr;
     std::map<std::string, GraphEntry> graphs;
     uint64_t stamp = 0;
     uint64_t timeout_ns = 2000000000ull;
@@ -566,6 +569,7 @@ nb_status nb_create(nb_ctx **out, int device, const nb_params *p) {
     cudaDeviceProp prop;
     if (cudaSetDevice(device) != cudaSuccess || cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&ctx->err_word, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->err_word, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -590,11 +594,14 @@ void nb_destroy(nb_ctx *ctx) {
                       &ctx->vals,  &ctx->red,   &ctx->traj,  &ctx->traj64,   &ctx->st_x,     &ctx->st_v,
                       &ctx->abar64, &ctx->stage[0], &ctx->stage[1], &ctx->stage[2], &ctx->stage[3],
                       &ctx->tune[0], &ctx->tune[1], &ctx->tune[2], &ctx->tune[3], &ctx->tune[4],
-                      &ctx->tune[5], &ctx->bat};
+                      &ctx->tune[5], &ctx->bat, &ctx->adj_traj[0], &ctx->adj_traj[1],
+                      &ctx->adj_traj64[0], &ctx->adj_traj64[1], &ctx->adj_x[0], &ctx->adj_x[1],
+                      &ctx->adj_v[0], &ctx->adj_v[1], &ctx->part2, &ctx->counters2};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->err_word) cudaFree(ctx->err_word);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->side2) cudaStreamDestroy(ctx->side2);
     cudaGetLastError();
     delete ctx;
 }
@@ -792,18 +799,23 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
     Plan pf, pv;
     NB_TRY(make_plan(ctx, sf, n, &pf));
     NB_TRY(make_plan(ctx, sv, n, &pv));
-    NB_TRY(ensure(ctx, ctx->part, std::max(pf.part_bytes, pv.part_bytes)));
-    NB_TRY(ensure(ctx, ctx->counters, (size_t)std::max(pf.iblocks, pv.iblocks) * 4, true));
+    // the reverse sweep (stream side) and the recompute of the previous
+    // segment (stream side2) run concurrently, each with its own split scratch
+    NB_TRY(ensure(ctx, ctx->part, pv.part_bytes));
+    NB_TRY(ensure(ctx, ctx->counters, (size_t)pv.iblocks * 4, true));
+    NB_TRY(ensure(ctx, ctx->part2, pf.part_bytes));
+    NB_TRY(ensure(ctx, ctx->counters2, (size_t)pf.iblocks * 4, true));
     const int64_t npad = pf.npad;
     const int k = ckpt_every;
-    NB_TRY(ensure(ctx, ctx->traj, (size_t)(k + 1) * npad * 16));
-    NB_TRY(ensure(ctx, ctx->rec, (size_t)npad * 8 * pol_rec_f4(sv.pol)));
     const bool f64 = f64_state(ctx);
-    if (f64) NB_TRY(ensure(ctx, ctx->traj64, (size_t)k * n * 48));
-    NB_TRY(ensure(ctx, ctx->st_x, b3));
-    NB_TRY(ensure(ctx, ctx->st_v, b3));
+    NB_TRY(ensure(ctx, ctx->rec, (size_t)npad * 8 * pol_rec_f4(sv.pol)));
+    for (int b = 0; b < 2; ++b) {
+        NB_TRY(ensure(ctx, ctx->adj_traj[b], (size_t)(k + 1) * npad * 16));
+        if (f64) NB_TRY(ensure(ctx, ctx->adj_traj64[b], (size_t)k * n * 48));
+        NB_TRY(ensure(ctx, ctx->adj_x[b], b3));
+        NB_TRY(ensure(ctx, ctx->adj_v[b], b3));
+    }
     NB_TRY(ensure(ctx, ctx->abar64, (size_t)n * 24));
-    float4 *traj = (float4 *)ctx->traj.p;
     const size_t slot_bytes = (size_t)n * 6 * es;
     const int nseg = steps / k;
 
@@ -817,35 +829,58 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
         int64_t saved = ctx->launches;
         nb_status rs = NB_OK;
-        for (int seg = nseg - 1; rs == NB_OK && seg >= 0; --seg) {
-            // 1) restore checkpoint seg into scratch state, pack x_t0
+        std::vector<cudaEvent_t> events;
+        auto new_event = [&](cudaEvent_t *e) -> bool {
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+            events.push_back(*e);
+            return true;
+        };
+        auto cuda_ok = [&](cudaError_t ce) -> bool {
+            if (ce == cudaSuccess) return true;
+            rs = fail(ctx, NB_ERR_CUDA, "adjoint capture: %s", cudaGetErrorString(ce));
+            return false;
+        };
+        std::vector<cudaEvent_t> ev_rec(nseg), ev_swp(nseg);
+        auto traj_slot = [&](int b, int t) {
+            return (float4 *)ctx->adj_traj[b].p + (size_t)t * (npad / 2) * 2;
+        };
+        // Recompute segment `seg` from its checkpoint on side2, keeping the
+        // packed positions of every step (and FP64 ones in the precision form).
+        auto recompute = [&](int seg) {
+            const int b = seg & 1;
             const char *slot = (const char *)ckpt + (size_t)seg * slot_bytes;
-            cudaError_t ce = launch_copy_ckpt_state(n, f64_state(ctx) ? 1 : 0, slot, ctx->st_x.p,
-                                                    ctx->st_v.p, ctx->side);
-            if (ce != cudaSuccess) { rs = fail(ctx, NB_ERR_CUDA, "%s", cudaGetErrorString(ce)); break; }
+            if (!cuda_ok(launch_copy_ckpt_state(n, f64 ? 1 : 0, slot, ctx->adj_x[b].p,
+                                                ctx->adj_v[b].p, ctx->side2)))
+                return;
             ctx->launches += 1;
-            rs = pack(ctx, n, npad, ctx->st_x.p, nullptr, m, traj, nullptr, ctx->side);
-            // 2) recompute the segment forward, keeping every x_t packed
+            rs = pack(ctx, n, npad, ctx->adj_x[b].p, nullptr, m, traj_slot(b, 0), nullptr, ctx->side2);
             for (int t = 0; rs == NB_OK && t < k - 1; ++t) {
-                ForceArgs a = base_args(ctx, pf, n, traj + (size_t)t * (npad / 2) * 2);
+                ForceArgs a = base_args(ctx, pf, n, traj_slot(b, t));
+                a.part = (float4 *)ctx->part2.p;
+                a.counters = (unsigned *)ctx->counters2.p;
                 a.op = kEpiKickDrift;
-                a.x = ctx->st_x.p;
-                a.v = ctx->st_v.p;
-                a.xm_next = traj + (size_t)(t + 1) * (npad / 2) * 2;
-                // precision form: keep the FP64 positions of every step (slot t+1)
-                if (f64) a.ckpt = (char *)ctx->traj64.p + (size_t)(t + 1) * n * 48;
-                rs = launch_force(ctx, pf, a, ctx->side);
+                a.x = ctx->adj_x[b].p;
+                a.v = ctx->adj_v[b].p;
+                a.xm_next = traj_slot(b, t + 1);
+                if (f64) a.ckpt = (char *)ctx->adj_traj64[b].p + (size_t)(t + 1) * n * 48;
+                rs = launch_force(ctx, pf, a, ctx->side2);
             }
-            // 3) sweep the segment backwards
+            if (rs == NB_OK && (!new_event(&ev_rec[seg]) || !cuda_ok(cudaEventRecord(ev_rec[seg], ctx->side2))))
+                if (rs == NB_OK) rs = fail(ctx, NB_ERR_CUDA, "adjoint capture: event");
+        };
+        // Sweep segment `seg` backwards on side.
+        auto sweep = [&](int seg) {
+            const int b = seg & 1;
+            if (!cuda_ok(cudaStreamWaitEvent(ctx->side, ev_rec[seg], 0))) return;
+            const char *slot = (const char *)ckpt + (size_t)seg * slot_bytes;
             for (int t = k - 1; rs == NB_OK && t >= 0; --t) {
-                const float4 *xm_t = traj + (size_t)t * (npad / 2) * 2;
                 const double *x64 = !f64 ? nullptr
                                     : t == 0 ? (const double *)slot
-                                             : (const double *)((char *)ctx->traj64.p + (size_t)t * n * 48);
-                ce = launch_adj_prepare(n, npad, f64 ? 1 : 0, xm_t, x64, 6, m, vbar0, xbar0,
-                                        ctx->p.dt, (float4 *)ctx->rec.p,
-                                        (double *)ctx->abar64.p, ctx->side);
-                if (ce != cudaSuccess) { rs = fail(ctx, NB_ERR_CUDA, "%s", cudaGetErrorString(ce)); break; }
+                                             : (const double *)((char *)ctx->adj_traj64[b].p + (size_t)t * n * 48);
+                if (!cuda_ok(launch_adj_prepare(n, npad, f64 ? 1 : 0, traj_slot(b, t), x64, 6, m, vbar0,
+                                                xbar0, ctx->p.dt, (float4 *)ctx->rec.p,
+                                                (double *)ctx->abar64.p, ctx->side)))
+                    return;
                 ctx->launches += 1;
                 ForceArgs a = base_args(ctx, pv, n, (const float4 *)ctx->rec.p);
                 a.op = kEpiVjp;
@@ -855,13 +890,33 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
                 a.mass = m;
                 rs = launch_force(ctx, pv, a, ctx->side);
             }
+            if (rs == NB_OK && (!new_event(&ev_swp[seg]) || !cuda_ok(cudaEventRecord(ev_swp[seg], ctx->side))))
+                if (rs == NB_OK) rs = fail(ctx, NB_ERR_CUDA, "adjoint capture: event");
+        };
+        cudaEvent_t fork;
+        if (!new_event(&fork) || !cuda_ok(cudaEventRecord(fork, ctx->side)) ||
+            !cuda_ok(cudaStreamWaitEvent(ctx->side2, fork, 0))) {
+            if (rs == NB_OK) rs = fail(ctx, NB_ERR_CUDA, "adjoint capture: fork");
+        }
+        if (rs == NB_OK) recompute(nseg - 1);
+        for (int seg = nseg - 1; rs == NB_OK && seg >= 0; --seg) {
+            if (seg >= 1) {
+                // segment seg-1 reuses the buffers of segment seg+1
+                if (seg + 1 <= nseg - 1 && !cuda_ok(cudaStreamWaitEvent(ctx->side2, ev_swp[seg + 1], 0)))
+                    break;
+                recompute(seg - 1);
+                if (rs != NB_OK) break;
+            }
+            sweep(seg);
         }
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamEndCapture(ctx->side, &graph);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
         int64_t nodes = ctx->launches - saved;
         ctx->launches = saved;
         if (rs != NB_OK) {
             if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
             return rs;
         }
         if (ce != cudaSuccess) return fail(ctx, NB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));

@@ -19,7 +19,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=65536)
     ap.add_argument("--shape", default="0,0,0,0", help="threads,bodies_per_thread,split,jtile (0 = auto)")
-    ap.add_argument("--pol", default="fp32", choices=["fp32", "comp", "vjp", "vjp-comp", "energy"])
+    ap.add_argument("--pol", default="fp32",
+                    choices=["fp32", "comp", "vjp", "vjp-comp", "energy", "step", "step-comp"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--peaks", action="store_true")
     a = ap.parse_args()
@@ -36,7 +37,7 @@ def main():
         print(json.dumps({"runs": runs, "best": {k: max(r[k] for r in runs) for k in runs[0]}}))
         return
     shape = tuple(int(v) for v in a.shape.split(","))
-    prec = "comp" if a.pol in ("comp", "vjp-comp") else "fp32"
+    prec = "comp" if a.pol in ("comp", "vjp-comp", "step-comp") else "fp32"
     f = torch.float64 if prec == "comp" else torch.float32
     dev = torch.device("cuda:0")
     s = ics.plummer(a.n, seed=1)
@@ -44,13 +45,15 @@ def main():
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,
-            "energy": MODE_POTENTIAL}[a.pol]
+            "energy": MODE_POTENTIAL, "step": MODE_FORWARD, "step-comp": MODE_FORWARD}[a.pol]
 
     def call():
         if a.pol in ("fp32", "comp"):
             ctx.accel(x, m)
         elif a.pol in ("vjp", "vjp-comp"):
             ctx.vjp(x, m, ab)
+        elif a.pol in ("step", "step-comp"):
+            ctx.run(x, v, m, 1)  # one paper step: pack + force sum with the kick/drift epilogue
         else:
             ctx.energy(x, v, m)
 
