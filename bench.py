@@ -324,11 +324,13 @@ def extras(ctx0, torch, dev, np):
     c = Context(1.0, 0.01, 1e-3, device=dev.index)
     xb, vb, mb = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (bx, bv, bm))
     offt = torch.tensor(off, dtype=torch.int64)
+    c.autotune_batched(offt)  # tile / gang shape from the project's tuner
     c.run_batched(offt, xb.clone(), vb.clone(), mb, 1)  # plan + capture
     t = _timed(torch, dev, lambda: c.run_batched(offt, xb, vb, mb, 100))
     sizes = np.diff(off).astype(np.float64)
     out["c4_batched"] = {"systems": 512, "bodies": int(off[-1]), "steps": 100,
-                         "interactions_per_s": float((sizes ** 2).sum()) * 100 / t, "s": t}
+                         "interactions_per_s": float((sizes ** 2).sum()) * 100 / t, "s": t,
+                         "shape": c.get_batched_config(offt)}
     c.close()
     # C5: adjoint, N = 16384 cube (seed 4), T = 200, checkpoint every 20
     n, T, k = 16384, 200, 20

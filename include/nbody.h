@@ -142,6 +142,19 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
 int64_t nb_batched_max_n(void);
 
 /*
+ * Autotune nb_run_batched for this size profile (synchronous): times a few
+ * steps of every candidate (bodies per thread, j-tile, largest gang of CTAs
+ * per system) on synthetic bodies with the same system sizes and keeps the
+ * fastest for later nb_run_batched calls with the same sizes.
+ */
+nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets);
+
+/* The batched launch the context would use for these sizes: out[0..5] =
+ * {threads per CTA, bodies per thread, j-tile bodies, largest gang, CTAs in
+ * the persistent grid, 1 if the shape came from nb_autotune_batched}. */
+nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6);
+
+/*
  * Reverse mode of nb_run with the paper scheme. Given the checkpoints written
  * by nb_run(..., ckpt, ckpt_every) over `steps` steps and the cotangents of
  * the final state (xbar_T, vbar_T: [n][3]), writes the gradients of the same

@@ -91,6 +91,7 @@ struct nb_ctx {
     int debug = 0;
     int64_t launches = 0;
     std::map<std::string, TuneEntry> tuned;
+    std::map<uint64_t, BatchPlan> batched_tuned;  // size profile -> tuned batched shape
     std::string tune_path;
 };
 
@@ -472,6 +473,46 @@ nb_status sync_and_check(nb_ctx *ctx, cudaStream_t st) {
                     "device-side wait gave up (error bits 0x%x: 1 tile wait, 2 slot wait, "
                     "4 copy drain, 8 gang barrier); results of the affected calls are invalid",
                     h);
+    }
+    return NB_OK;
+}
+
+// FNV-1a over the system sizes: the key of the batched tuning table.
+uint64_t sizes_signature(const std::vector<int64_t> &off) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t s = 1; s < off.size(); ++s) {
+        uint64_t v = (uint64_t)(off[s] - off[s - 1]);
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    }
+    return h;
+}
+
+// Offsets may live on the host or the device; validate them.
+nb_status read_offsets(nb_ctx *ctx, int nsys, const int64_t *offsets, cudaStream_t st,
+                       std::vector<int64_t> &off) {
+    off.assign((size_t)nsys + 1, 0);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, offsets);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, NB_ERR_INVALID, "offsets: cannot query pointer");
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        NB_CUDA(cudaStreamSynchronize(st));
+        NB_CUDA(cudaMemcpy(off.data(), offsets, off.size() * 8, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(off.data(), offsets, off.size() * 8);
+    }
+    if (off[0] != 0) return fail(ctx, NB_ERR_INVALID, "offsets[0] must be 0");
+    for (int s = 0; s < nsys; ++s) {
+        const int64_t ns = off[s + 1] - off[s];
+        if (ns < 0) return fail(ctx, NB_ERR_INVALID, "offsets must be non-decreasing");
+        if (ns > batched_max_n())
+            return fail(ctx, NB_ERR_INVALID, "system %d has %lld bodies, above the limit %lld", s,
+                        (long long)ns, (long long)batched_max_n());
     }
     return NB_OK;
 }
@@ -944,28 +985,8 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
         return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs use the paper scheme");
     if (!offsets) return fail(ctx, NB_ERR_INVALID, "offsets is NULL");
     NB_CUDA(cudaSetDevice(ctx->device));
-    // offsets may live on the host or the device
-    std::vector<int64_t> off((size_t)nsys + 1);
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, offsets);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, NB_ERR_INVALID, "offsets: cannot query pointer");
-    }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
-        NB_CUDA(cudaStreamSynchronize(as_stream(stream)));
-        NB_CUDA(cudaMemcpy(off.data(), offsets, off.size() * 8, cudaMemcpyDeviceToHost));
-    } else {
-        memcpy(off.data(), offsets, off.size() * 8);
-    }
-    if (off[0] != 0) return fail(ctx, NB_ERR_INVALID, "offsets[0] must be 0");
-    for (int s = 0; s < nsys; ++s) {
-        const int64_t ns = off[s + 1] - off[s];
-        if (ns < 0) return fail(ctx, NB_ERR_INVALID, "offsets must be non-decreasing");
-        if (ns > batched_max_n())
-            return fail(ctx, NB_ERR_INVALID, "system %d has %lld bodies, above the limit %lld", s,
-                        (long long)ns, (long long)batched_max_n());
-    }
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, as_stream(stream), off));
     const int64_t total = off[nsys];
     if (total == 0) return NB_OK;
     NB_TRY(check_ptr(ctx, x, 4, "x", nullptr));
@@ -973,6 +994,13 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     NB_TRY(check_ptr(ctx, m, 4, "m", nullptr));
     cudaStream_t st = as_stream(stream);
     BatchPlan plan;
+    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
+    if (tuned != ctx->batched_tuned.end()) {
+        plan.nt = tuned->second.nt;
+        plan.r = tuned->second.r;
+        plan.jt = tuned->second.jt;
+        plan.gmax = tuned->second.gmax;
+    }
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
         return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
@@ -1004,6 +1032,90 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     }
     NB_CUDA(cudaGraphLaunch(g->exec, st));
     ctx->launches += g->nodes;
+    return NB_OK;
+}
+
+nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    const int64_t total = off[nsys];
+    if (total == 0) return NB_OK;
+    NB_TRY(ensure(ctx, ctx->tune[1], (size_t)total * 12));
+    NB_TRY(ensure(ctx, ctx->tune[2], (size_t)total * 12));
+    NB_TRY(ensure(ctx, ctx->tune[3], (size_t)total * 4));
+    cudaStream_t st = ctx->side;
+    cudaEvent_t e0, e1;
+    NB_CUDA(cudaEventCreate(&e0));
+    NB_CUDA(cudaEventCreate(&e1));
+    const int probe_steps = 4;
+    float best_ms = 1e30f;
+    BatchPlan best;
+    for (int r : {1, 2, 4}) {
+        for (int jt : {64, 128}) {
+            for (int gmax : {8, 16}) {
+                BatchPlan plan;
+                plan.r = r;
+                plan.jt = jt;
+                plan.gmax = gmax;
+                std::string why;
+                if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
+                NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
+                NB_CUDA(batched_upload(plan, ctx->bat.p, st));
+                float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
+                NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
+                const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
+                NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, eps2, (float)ctx->p.G,
+                                        (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+                NB_CUDA(cudaEventRecord(e0, st));
+                NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, eps2, (float)ctx->p.G,
+                                        (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+                NB_CUDA(cudaEventRecord(e1, st));
+                NB_CUDA(cudaEventSynchronize(e1));
+                ctx->launches += 6;
+                float ms = 0.f;
+                NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = plan;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    NB_TRY(sync_and_check(ctx, st));
+    if (best_ms >= 1e30f) return fail(ctx, NB_ERR_CUDA, "no batched shape could be planned");
+    ctx->batched_tuned[sizes_signature(off)] = best;
+    clear_graphs(ctx);
+    return NB_OK;
+}
+
+nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6) {
+    if (!ctx || !out6) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    BatchPlan plan;
+    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
+    const bool from_tune = tuned != ctx->batched_tuned.end();
+    if (from_tune) {
+        plan.r = tuned->second.r;
+        plan.jt = tuned->second.jt;
+        plan.gmax = tuned->second.gmax;
+    }
+    std::string why;
+    if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
+        return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
+    out6[0] = plan.nt;
+    out6[1] = plan.r;
+    out6[2] = plan.jt;
+    out6[3] = plan.gmax;
+    out6[4] = plan.ncta;
+    out6[5] = from_tune ? 1 : 0;
     return NB_OK;
 }
 

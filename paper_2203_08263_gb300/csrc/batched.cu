@@ -213,6 +213,24 @@ __global__ void batched_pack_kernel(const int64_t *off, const int64_t *poff, int
     }
 }
 
+__global__ void batched_fill_kernel(const int64_t *off, float *x, float *v, float *m) {
+    const int s = blockIdx.x;
+    const int64_t b0 = off[s], n = off[s + 1] - b0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t g = b0 + i;
+        for (int c = 0; c < 3; ++c) {
+            uint32_t h = (uint32_t)(g * 3 + c) * 2654435761u;
+            h ^= h >> 15;
+            h *= 0x2c1b3c6dU;
+            h ^= h >> 12;
+            const float u = (float)(h >> 8) * (1.0f / 16777216.0f);
+            x[3 * g + c] = 2.f * u - 1.f;
+            v[3 * g + c] = 0.1f * (u - 0.5f);
+        }
+        m[g] = 1.0f / (float)n;
+    }
+}
+
 template <int NT, int R>
 size_t batched_smem(int jt) {
     return 128 + (size_t)kStages * jt * 16;
@@ -306,7 +324,7 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
     p.total_pad = std::max<int64_t>(acc, p.jt);
 
     // gang sizes and LPT assignment under a makespan bound T (bisection)
-    const int gmax = std::min(16, P);
+    const int gmax = std::max(1, std::min(p.gmax > 0 ? p.gmax : 16, P));
     std::vector<int> sizes;
     for (int g = 1; g <= gmax; g *= 2) sizes.push_back(g);
     double lb = 0.0, work = 0.0;
@@ -409,6 +427,7 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
     mix((uint64_t)p.r);
     mix((uint64_t)p.jt);
     mix((uint64_t)p.ncta);
+    mix((uint64_t)p.gmax);
     p.signature = h;
     return true;
 }
@@ -430,6 +449,14 @@ cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
     NB_UP(gang_size, L.o_gs)
 #undef NB_UP
     return cudaSuccess;
+}
+
+cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, float *x, float *v,
+                                   float *m, cudaStream_t st) {
+    Layout L = layout_of(p);
+    batched_fill_kernel<<<p.nsys, 256, 0, st>>>((const int64_t *)((char *)scratch + L.o_off), x, v,
+                                                m);
+    return cudaGetLastError();
 }
 
 cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *v, const float *m,

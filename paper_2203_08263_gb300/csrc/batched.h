@@ -15,6 +15,7 @@ namespace nb {
 struct BatchPlan {
     int nsys = 0;
     int nt = 128, r = 2, jt = 64;   // kernel shape
+    int gmax = 16;                  // largest gang (CTAs sharing one system)
     int ncta = 0, ngang = 0;
     int64_t total = 0, total_pad = 0;
     std::vector<int64_t> off, poff;
@@ -36,6 +37,10 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
 // Upload the plan into `scratch` (on `st`) and enqueue: zero the gang
 // counters, pack all systems, launch the persistent kernel.
 cudaError_t batched_upload(const BatchPlan &plan, void *scratch, cudaStream_t st);
+// Deterministic synthetic state for tuning runs (positions in [-1,1]^3,
+// small velocities, masses 1/N_s): timing does not depend on the values.
+cudaError_t batched_fill_synthetic(const BatchPlan &plan, void *scratch, float *x, float *v,
+                                   float *m, cudaStream_t st);
 cudaError_t batched_enqueue(const BatchPlan &plan, void *scratch, float *x, float *v,
                             const float *m, int steps, float eps2, float G, float dt, int *err,
                             uint64_t timeout_ns, cudaStream_t st);

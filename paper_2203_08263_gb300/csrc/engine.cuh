@@ -31,7 +31,7 @@ namespace nb {
 #define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR(unroll n))
 
 #ifndef NB_PRODUCER_WARP
-#define NB_PRODUCER_WARP 1  // 1: a dedicated warp issues the copies; 0: consumer thread 0 does
+#define NB_PRODUCER_WARP 0  // 0: consumer thread 0 issues the copies; 1: a dedicated warp does
 #endif
 
 constexpr int kStages = 4;        // ring depth

@@ -45,6 +45,8 @@ SIGNATURES = {
     "nb_run": (_i, [_vp, _i64, _vp, _vp, _vp, _i, _vp, _i, _vp]),
     "nb_run_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _vp]),
     "nb_batched_max_n": (_i64, []),
+    "nb_autotune_batched": (_i, [_vp, _i, _vp]),
+    "nb_get_batched_config": (_i, [_vp, _i, _vp, _c.POINTER(_i)]),
     "nb_adjoint": (_i, [_vp, _i64, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_vjp": (_i, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_energy": (_i, [_vp, _i64, _vp, _vp, _vp, _c.POINTER(_d), _vp]),
@@ -190,6 +192,17 @@ class Context:
         nsys = int(offsets.shape[0]) - 1
         self._check(self.lib.nb_run_batched(self.h, nsys, _ptr(offsets), _ptr(x), _ptr(v), _ptr(m),
                                             int(steps), self._s(stream)), "nb_run_batched")
+
+    def autotune_batched(self, offsets):
+        self._check(self.lib.nb_autotune_batched(self.h, int(offsets.shape[0]) - 1, _ptr(offsets)),
+                    "nb_autotune_batched")
+
+    def get_batched_config(self, offsets) -> dict:
+        out = (_i * 6)()
+        self._check(self.lib.nb_get_batched_config(self.h, int(offsets.shape[0]) - 1, _ptr(offsets), out),
+                    "nb_get_batched_config")
+        return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "gang_max": out[3],
+                "ctas": out[4], "tuned": bool(out[5])}
 
     # ---- reverse
     def vjp(self, x, m, abar, stream=None):

@@ -59,6 +59,25 @@ def test_ragged_and_empty_systems_device_offsets(nbm):
         assert rel_l2(gx[a:b], xr) <= 1e-5, s
 
 
+def test_autotuned_batched_shape(nbm):
+    off, x, v, m = ics.ensemble(nsys=60, seed=21, nmin=64, nmax=2048)
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    offt = torch.tensor(off, dtype=torch.int64)
+    assert not ctx.get_batched_config(offt)["tuned"]
+    ctx.autotune_batched(offt)
+    cfg = ctx.get_batched_config(offt)
+    assert cfg["tuned"] and cfg["bodies_per_thread"] in (1, 2, 4) and cfg["jtile"] in (64, 128)
+    xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float32, device=DEV)
+    ctx.run_batched(offt, xt, vt, mt, 4)
+    ctx.sync()
+    for s in (0, 17, 59):
+        a, b = off[s], off[s + 1]
+        xr, _ = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 4)
+        assert rel_l2(to_np(xt)[a:b], xr) <= 1e-5
+
+
 def test_c4_full_ensemble_sampled(nbm):
     """Batched ensemble: 512 cube systems, N log-uniform in [64, 8192]
     (seed 3), eps=0.01, dt=1e-3, 100 steps in one persistent launch; the
