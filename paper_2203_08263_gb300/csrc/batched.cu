@@ -2,10 +2,10 @@
 // paper steps inside one cooperative launch. CTAs are grouped in gangs; a
 // gang walks its list of systems, and for each step every member computes the
 // forces on its slice of i-bodies from all j-bodies of the system (j-tiles
-// streamed by bulk copies through the same shared-memory ring as the
-// single-system kernel), applies the half kick and the drift, writes the
-// repacked positions to the other buffer and meets the rest of the gang at a
-// bounded global-memory barrier before the next step.
+// streamed by 1-D bulk copies, issued by thread 0, through a shared-memory
+// ring as in the single-system kernel), applies the half kick and the drift,
+// writes the repacked positions to the other buffer and meets the rest of the
+// gang at a bounded global-memory barrier before the next step.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -66,14 +66,13 @@ __device__ void gang_barrier(unsigned *ctr, unsigned target, uint64_t timeout_ns
 }
 
 template <int NT, int R>
-__global__ void __launch_bounds__(NT + 32, 1) batched_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + kStages;
     float4 *ring = reinterpret_cast<float4 *>(smem_raw + 128);
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const bool producer = warp == NT / 32;
+    const int lane = tid & 31;
     const int gang = a.cta_gang[blockIdx.x];
     const int rank = a.cta_rank[blockIdx.x];
     const int gsz = a.gang_size[gang];
@@ -91,10 +90,26 @@ __global__ void __launch_bounds__(NT + 32, 1) batched_kernel(const BatchArgs a) 
     }
     __syncthreads();
 
-    uint32_t kk = 0;       // tiles streamed so far by this CTA (ring position)
+    // Ring position q (tiles streamed so far by this CTA) runs on across
+    // passes, steps and systems; slot q % kStages, phase q / kStages. Thread 0
+    // issues position q once position q - kStages has been released.
+    uint32_t kk = 0;       // position of the current pass's first tile
+    uint32_t issued = 0;   // positions issued so far (thread 0)
     unsigned epoch = 0;    // gang barriers passed
-    int issued_total = 0;  // producer: copies issued
-    bool give_up = false;  // a wait failed: stop streaming, keep barriers
+    bool give_up = false;  // a wait failed: stop streaming, keep the barriers
+
+    auto issue = [&](uint32_t q, const float4 *src_tile) {
+        const int slot = q % kStages;
+        if (q >= (uint32_t)kStages &&
+            !mbar_wait(&empty[slot], ((q / kStages) - 1) & 1, a.timeout_ns)) {
+            atomicOr(a.err, kErrEmptyWait);
+            give_up = true;
+            return;
+        }
+        mbar_arrive_expect_tx(&full[slot], tile_bytes);
+        bulk_g2s(ring + slot * f4_per_tile, src_tile, tile_bytes, &full[slot]);
+        issued = q + 1;
+    };
 
     for (int w = a.gang_first[gang]; w < a.gang_first[gang + 1]; ++w) {
         const int s = a.work[w];
@@ -108,49 +123,35 @@ __global__ void __launch_bounds__(NT + 32, 1) batched_kernel(const BatchArgs a) 
         const int64_t hi = lo + chunk < n ? lo + chunk : n;
         const int passes = hi > lo ? (int)((hi - lo + (int64_t)NT * R - 1) / ((int64_t)NT * R)) : 0;
         for (int t = 0; t < a.steps; ++t) {
-            const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // pair layout: 2 float4 per 2 bodies
+            const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
             float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
+            if (tid == 0) fence_proxy_async_global();
             for (int ps = 0; ps < passes; ++ps) {
-                if (producer) {
-                    if (lane == 0) {
-                        fence_proxy_async_global();
-                        for (int k = 0; k < ntl && !give_up; ++k, ++kk) {
-                            const int slot = kk % kStages;
-                            if (kk >= (uint32_t)kStages &&
-                                !mbar_wait(&empty[slot], ((kk / kStages) - 1) & 1, a.timeout_ns)) {
-                                atomicOr(a.err, kErrEmptyWait);
-                                give_up = true;
-                                break;
-                            }
-                            mbar_arrive_expect_tx(&full[slot], tile_bytes);
-                            bulk_g2s(ring + slot * f4_per_tile, src + (int64_t)k * f4_per_tile,
-                                     tile_bytes, &full[slot]);
-                            ++issued_total;
-                        }
-                    }
-                    __syncwarp();
-                } else {
-                    const int64_t ibase = lo + (int64_t)ps * NT * R;
-                    AccelF32x2::I ist[R];
-                    AccelF32x2::T tot[R];
-                    AccelF32x2::C cst;
-                    cst.eps2 = dup(a.eps2);
+                if (tid == 0 && !give_up)
+                    for (int k = 0; k < ntl && k < kStages - 1 && !give_up; ++k)
+                        issue(kk + k, src + (int64_t)k * f4_per_tile);
+                const int64_t ibase = lo + (int64_t)ps * NT * R;
+                AccelF32x2::I ist[R];
+                AccelF32x2::T tot[R];
+                AccelF32x2::C cst;
+                cst.eps2 = dup(a.eps2);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        int64_t i = ibase + r * NT + tid;
-                        if (i >= hi) i = lo;
-                        ist[r].nx = dup(-pair_get(src, i, 0));
-                        ist[r].ny = dup(-pair_get(src, i, 1));
-                        ist[r].nz = dup(-pair_get(src, i, 2));
-                        AccelF32x2::zero_total(tot[r]);
+                for (int r = 0; r < R; ++r) {
+                    int64_t i = ibase + r * NT + tid;
+                    if (i >= hi) i = lo;
+                    ist[r].nx = dup(-pair_get(src, i, 0));
+                    ist[r].ny = dup(-pair_get(src, i, 1));
+                    ist[r].nz = dup(-pair_get(src, i, 2));
+                    AccelF32x2::zero_total(tot[r]);
+                }
+                for (int k = 0; k < ntl; ++k) {
+                    const uint32_t q = kk + k;
+                    const int slot = q % kStages;
+                    if (!give_up && !mbar_wait(&full[slot], (q / kStages) & 1, a.timeout_ns)) {
+                        atomicOr(a.err, kErrFullWait);
+                        give_up = true;
                     }
-                    for (int k = 0; k < ntl; ++k, ++kk) {
-                        const int slot = kk % kStages;
-                        if (give_up || !mbar_wait(&full[slot], (kk / kStages) & 1, a.timeout_ns)) {
-                            if (!give_up) atomicOr(a.err, kErrFullWait);
-                            give_up = true;
-                            continue;
-                        }
+                    if (!give_up) {
                         const float4 *tile = ring + slot * f4_per_tile;
 #pragma unroll 2
                         for (int jp = 0; jp < (a.jt >> 1); ++jp) {
@@ -161,26 +162,31 @@ __global__ void __launch_bounds__(NT + 32, 1) batched_kernel(const BatchArgs a) 
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&empty[slot]);
                     }
+                    // refill: position q + kStages - 1 goes into the slot of q - 1
+                    if (tid == 0 && !give_up && k + kStages - 1 < ntl)
+                        issue(q + kStages - 1, src + (int64_t)(k + kStages - 1) * f4_per_tile);
+                }
+                kk += ntl;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int64_t i = ibase + r * NT + tid;
-                        if (i < hi) {
-                            const float ax = a.G * (tot[r].x.x + tot[r].x.y);
-                            const float ay = a.G * (tot[r].y.x + tot[r].y.y);
-                            const float az = a.G * (tot[r].z.x + tot[r].z.y);
-                            float *xp = a.x + 3 * (b0 + i);
-                            float *vp = a.v + 3 * (b0 + i);
-                            const float acc[3] = {ax, ay, az};
-                            float xs[3];
+                for (int r = 0; r < R; ++r) {
+                    const int64_t i = ibase + r * NT + tid;
+                    if (i < hi) {
+                        const float ax = a.G * (tot[r].x.x + tot[r].x.y);
+                        const float ay = a.G * (tot[r].y.x + tot[r].y.y);
+                        const float az = a.G * (tot[r].z.x + tot[r].z.y);
+                        float *xp = a.x + 3 * (b0 + i);
+                        float *vp = a.v + 3 * (b0 + i);
+                        const float acc[3] = {ax, ay, az};
+                        float xs[3];
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                float vc = __fadd_rn(vp[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
-                                vp[c] = vc;
-                                xs[c] = __fadd_rn(xp[c], __fmul_rn(vc, dt));
-                                xp[c] = xs[c];
-                            }
-                            pair_put(dst, i, xs[0], xs[1], xs[2], pair_get(src, i, 3));
+                        for (int c = 0; c < 3; ++c) {
+                            // v += a dt/2 (the printed half kick); x += v dt
+                            float vc = __fadd_rn(vp[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
+                            vp[c] = vc;
+                            xs[c] = __fadd_rn(xp[c], __fmul_rn(vc, dt));
+                            xp[c] = xs[c];
                         }
+                        pair_put(dst, i, xs[0], xs[1], xs[2], pair_get(src, i, 3));
                     }
                 }
             }
@@ -191,9 +197,9 @@ __global__ void __launch_bounds__(NT + 32, 1) batched_kernel(const BatchArgs a) 
         }
     }
     // never leave while our own copies may still be landing
-    if (producer && lane == 0) {
-        for (int k = issued_total > kStages ? issued_total - kStages : 0; k < issued_total; ++k) {
-            if (!mbar_wait(&full[k % kStages], (k / kStages) & 1, kDrainTimeoutNs))
+    if (tid == 0) {
+        for (uint32_t q = issued > (uint32_t)kStages ? issued - kStages : 0; q < issued; ++q) {
+            if (!mbar_wait(&full[q % kStages], (q / kStages) & 1, kDrainTimeoutNs))
                 atomicOr(a.err, kErrDrain);
         }
     }
@@ -302,11 +308,11 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
     cudaError_t e;
     const size_t smem = batched_smem<128, 2>(p.jt);
     if (p.r == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 1>, 160, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 1>, 128, smem);
     else if (p.r == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 2>, 160, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 2>, 128, smem);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 4>, 160, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 4>, 128, smem);
     if (e != cudaSuccess || occ <= 0) {
         why = "occupancy query failed";
         return false;
@@ -492,7 +498,7 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3((unsigned)p.ncta);
-    cfg.blockDim = dim3((unsigned)p.nt + 32);
+    cfg.blockDim = dim3((unsigned)p.nt);
     cfg.dynamicSmemBytes = batched_smem<128, 2>(p.jt);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

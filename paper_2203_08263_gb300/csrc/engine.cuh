@@ -5,12 +5,14 @@
 // 32-byte record for the force sums: {x0,x1,y0,y1}, {z0,z1,m0,m1}) and padded
 // with zero-mass bodies to a multiple of the j-tile, so every j-tile is full
 // and padding contributes exactly 0. CTA b handles i-block b / S and j-split
-// b % S. Each of its NT consumer threads owns R i-bodies in registers; a
-// dedicated producer warp streams the split's j-tiles into a ring of shared
-// memory slots with 1-D bulk async copies (cp.async.bulk, completion counted
-// on an mbarrier per slot), and the consumers release slots through a second
-// mbarrier per slot. Every wait is bounded by a timeout and records an error
-// bit instead of hanging.
+// b % S. Each of its NT threads owns R i-bodies in registers; thread 0 also
+// streams the split's j-tiles into a ring of shared-memory slots with 1-D
+// bulk async copies (cp.async.bulk, completion counted on an mbarrier per
+// slot), refilling a slot one tile after every warp has released it through
+// a second mbarrier per slot. (Built with NB_PRODUCER_WARP=1, a dedicated
+// extra warp issues the copies instead; it costs a fifth more threads per
+// CTA and, at 128 registers, one CTA per SM.) Every wait is bounded by a
+// timeout and records an error bit instead of hanging.
 //
 // Split reduction. With S > 1 each CTA writes its partial sums, and the last
 // CTA of an i-block to finish (atomic ticket) adds the S partials in split
