@@ -35,6 +35,11 @@ UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 20  # the paper's convention (Section 4.1)
 
 
+def workload(n: int) -> str:
+    return (f"single system N={n} Plummer (seed 1), G=1, eps=0.05, dt=1e-3; "
+            "one bench step = one paper update (force sum + half kick + drift)")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,11 +161,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"single system N={n} Plummer (seed 1), eps=0.05, "
-                                                    f"one step; reference step = oracle force sum of {sample} "
-                                                    f"i-bodies x {n} j-bodies", "n": n},
+        "data": "synthetic", "config": {"workload": workload(n), "n": n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{sample} i-bodies x {n} j-bodies per step"},
+                         "sample": f"each step: the FP64 oracle's force sum for {sample} i-bodies "
+                                   f"against all {n} j-bodies (a bounded sample of one step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -262,9 +266,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"single system N={n} Plummer (seed 1), G=1, eps=0.05, dt=1e-3, FP32; "
-                               "one bench step = one paper update (half kick + drift)",
-                   "n": n, "l2": "flushed between steps (256 MiB write outside the timed events)",
+        "config": {"workload": workload(n), "n": n, "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "shape": cfg},
         "roofline": roofline,
         "interactions_per_s_per_gpu": inter * args.steps / (tot_ms / 1e3),

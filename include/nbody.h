@@ -217,7 +217,15 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out; with a short
  * timeout this exercises the error path without hanging (results are then
  * invalid and nb_sync returns NB_ERR_TIMEOUT). */
-typedef enum { NB_DBG_WAIT_TIMEOUT_NS = 1, NB_DBG_STALL_PRODUCER = 2 } nb_debug_key;
+typedef enum {
+    NB_DBG_WAIT_TIMEOUT_NS = 1,
+    NB_DBG_STALL_PRODUCER = 2,
+    /* FP32 forward denominator s^(3/2), s = r^2 + eps^2 (GPU analog of the
+     * paper's math-operation experiment, Sections 3.2.6 and 3.3.6):
+     * 0 = MUFU rsqrt cubed (default), 1 = IEEE sqrt then division,
+     * 2 = powf(s, -1.5). Tuned shapes apply to 0 only. */
+    NB_DBG_MATH_VARIANT = 3
+} nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 
 /*

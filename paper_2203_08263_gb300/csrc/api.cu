@@ -25,6 +25,8 @@ const ForceEntry *table_comp(int *count);
 const ForceEntry *table_pot(int *count);
 const ForceEntry *table_vjp(int *count);
 const ForceEntry *table_vjp_comp(int *count);
+const ForceEntry *table_div(int *count);
+const ForceEntry *table_pow(int *count);
 
 const ForceEntry *force_table(int pol, int *count) {
     switch (pol) {
@@ -34,6 +36,8 @@ const ForceEntry *force_table(int pol, int *count) {
         case kPolPot: return table_pot(count);
         case kPolVjp: return table_vjp(count);
         case kPolVjpComp: return table_vjp_comp(count);
+        case kPolDiv: return table_div(count);
+        case kPolPow: return table_pow(count);
         default: *count = 0; return nullptr;
     }
 }
@@ -89,6 +93,7 @@ struct nb_ctx {
     uint64_t stamp = 0;
     uint64_t timeout_ns = 2000000000ull;
     int debug = 0;
+    int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
     int64_t launches = 0;
     std::map<std::string, TuneEntry> tuned;
     std::map<uint64_t, BatchPlan> batched_tuned;  // size profile -> tuned batched shape
@@ -228,6 +233,8 @@ std::string tune_key(const nb_ctx *ctx, int mode, int64_t n) {
 }
 
 int mode_pol(const nb_ctx *ctx, int mode) {
+    if (mode == 0 && !f64_state(ctx) && ctx->math == 1) return kPolDiv;
+    if (mode == 0 && !f64_state(ctx) && ctx->math == 2) return kPolPow;
     if (mode == 0) return f64_state(ctx) ? kPolComp : kPolF32x2;
     if (mode == 1) return f64_state(ctx) ? kPolVjpComp : kPolVjp;
     return kPolPot;
@@ -252,6 +259,9 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n) {
     if (pol == kPolF32x2) {
         if (n >= 32768) { r = 4; jt = 128; }
         else if (n >= 4096) { r = 2; jt = 128; }
+    } else if (pol == kPolDiv || pol == kPolPow) {
+        r = 4;
+        if (n >= 4096) jt = 128;
     } else if (pol == kPolComp) {
         r = 2;
         if (n >= 4096) jt = 128;
@@ -282,7 +292,8 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
         return NB_OK;
     }
     auto it = ctx->tuned.find(tune_key(ctx, mode, n));
-    if (mode != 2 && it != ctx->tuned.end() && find_entry(it->second.pol, it->second.nt, it->second.r)) {
+    if (mode != 2 && ctx->math == 0 && it != ctx->tuned.end() &&
+        find_entry(it->second.pol, it->second.nt, it->second.r)) {
         const TuneEntry &t = it->second;
         *out = finish_shape(ctx, t.pol, t.nt, t.r, t.jt, t.split_mode, n);
         if (from_tune) *from_tune = true;
@@ -399,7 +410,7 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
     char key[512];
     snprintf(key, sizeof key, "run|%lld|%p|%p|%p|%d|%p|%d|%d.%d.%d.%d.%d|%llu|%d|%a|%a|%a",
              (long long)n, x, v, m, steps, ckpt, ckpt_every, s.pol, s.nt, s.r, s.split, s.jt,
-             (unsigned long long)ctx->timeout_ns * 4 + ctx->debug, ctx->p.scheme, ctx->p.G, ctx->p.eps, ctx->p.dt);
+             (unsigned long long)ctx->timeout_ns * 16 + ctx->debug * 4 + ctx->math, ctx->p.scheme, ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
@@ -1240,6 +1251,12 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
     if (key == NB_DBG_WAIT_TIMEOUT_NS) {
         if (value < 0) return fail(ctx, NB_ERR_INVALID, "timeout must be >= 0");
         ctx->timeout_ns = (uint64_t)value;
+        return NB_OK;
+    }
+    if (key == NB_DBG_MATH_VARIANT) {
+        if (value < 0 || value > 2) return fail(ctx, NB_ERR_INVALID, "math variant must be 0, 1 or 2");
+        ctx->math = (int)value;
+        clear_graphs(ctx);
         return NB_OK;
     }
     if (key == NB_DBG_STALL_PRODUCER) {

@@ -600,6 +600,56 @@ struct AccelScalar {
     }
 };
 
+// Ablation of the denominator (s^(3/2) with s = |d|^2 + eps^2), the GPU
+// analog of the paper's math-operation experiment (Sections 3.2.6, 3.3.6):
+//   kMath = 1: power then divide, w = m / (s * sqrt(s)) with IEEE sqrt and
+//              IEEE division (the listings' `dsquared ** -1.5` evaluated as
+//              a positive power and a division);
+//   kMath = 2: the power function, w = m * powf(s, -1.5).
+// Scalar FP32; otherwise identical to AccelScalar.
+template <int kMath>
+struct AccelMath {
+    static constexpr bool SELF_MASK = false;
+    static constexpr int REC_F4 = 2;
+    static constexpr int PART_F4 = 1;
+    static constexpr bool PER_TILE = false;
+    using I = AccelScalar::I;
+    using T = AccelScalar::T;
+    using A = T;
+    using F = AccelScalar::F;
+    using C = AccelScalar::C;
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = a.eps2; }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) { AccelScalar::load_i(a, i, s); }
+    __device__ static void zero_total(T &t) { t.x = t.y = t.z = 0.f; }
+    __device__ static void zero_acc(A &t) { zero_total(t); }
+    __device__ static void tile_done(A &, T &) {}
+    __device__ __forceinline__ static void one(float xj, float yj, float zj, float mj, const I &s,
+                                               T &t, float eps2) {
+        const float dx = xj + s.nx, dy = yj + s.ny, dz = zj + s.nz;
+        float q = fmaf(dx, dx, eps2);
+        q = fmaf(dy, dy, q);
+        q = fmaf(dz, dz, q);
+        float w;
+        if constexpr (kMath == 1)
+            w = __fdiv_rn(mj, __fmul_rn(q, __fsqrt_rn(q)));
+        else
+            w = mj * powf(q, -1.5f);
+        t.x = fmaf(w, dx, t.x);
+        t.y = fmaf(w, dy, t.y);
+        t.z = fmaf(w, dz, t.z);
+    }
+    __device__ __forceinline__ static void interact(const float4 (&rec)[2], const I &s, T &t,
+                                                    const C &c) {
+        one(rec[0].x, rec[0].z, rec[1].x, rec[1].z, s, t, c.eps2);
+        one(rec[0].y, rec[0].w, rec[1].y, rec[1].w, s, t, c.eps2);
+    }
+    __device__ static void to_part(const T &t, float4 *dst) { AccelScalar::to_part(t, dst); }
+    __device__ static void zero_final(F &f) { AccelScalar::zero_final(f); }
+    __device__ static void add_part(F &f, const float4 *src) { AccelScalar::add_part(f, src); }
+    __device__ static void from_total(F &f, const T &t) { AccelScalar::from_total(f, t); }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) { AccelScalar::finish(a, i, f); }
+};
+
 // Precision form: FP32 pair terms with one Newton-Raphson refinement of the
 // MUFU reciprocal square root (y <- y (3/2 - s y^2 / 2)), plain FP32 sums
 // within a j-tile, and the per-tile sums folded into a (hi, lo) pair with

@@ -16,7 +16,9 @@ enum Pol : int {
     kPolPot = 3,     // softened potential (diagnostics)
     kPolVjp = 4,     // adjoint VJP, FP32 state
     kPolVjpComp = 5, // adjoint VJP, compensated, FP64 state
-    kPolCount = 6
+    kPolDiv = 6,     // ablation: sqrt + division
+    kPolPow = 7,     // ablation: powf
+    kPolCount = 8
 };
 
 struct Shape {
