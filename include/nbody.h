@@ -133,7 +133,9 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * graph). System s owns bodies [offsets[s], offsets[s+1]); offsets (int64,
  * nsys+1 entries, offsets[0] = 0, non-decreasing) may be a host or a device
  * pointer. Systems do not interact. Each system's size must be at most
- * nb_batched_max_n(). FP32 precision only.
+ * nb_batched_max_n(); steps at most 2^20 per call. FP32 precision only.
+ * Inside the launch, work items (system, step, chunk of i-bodies) are taken
+ * from one queue; a step of a system starts when its previous step is done.
  */
 nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
                          const void *m, int steps, void *stream);
@@ -143,15 +145,16 @@ int64_t nb_batched_max_n(void);
 
 /*
  * Autotune nb_run_batched for this size profile (synchronous): times a few
- * steps of every candidate (bodies per thread, j-tile, largest gang of CTAs
- * per system) on synthetic bodies with the same system sizes and keeps the
- * fastest for later nb_run_batched calls with the same sizes.
+ * steps of every candidate (bodies per thread, j-tile) on synthetic bodies
+ * with the same system sizes and keeps the fastest for later nb_run_batched
+ * calls with the same sizes.
  */
 nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets);
 
 /* The batched launch the context would use for these sizes: out[0..5] =
- * {threads per CTA, bodies per thread, j-tile bodies, largest gang, CTAs in
- * the persistent grid, 1 if the shape came from nb_autotune_batched}. */
+ * {threads per CTA, bodies per thread, j-tile bodies, work items per step,
+ * CTAs in the persistent grid, 1 if the shape came from
+ * nb_autotune_batched}. */
 nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6);
 
 /*

@@ -1000,6 +1000,7 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     NB_TRY(read_offsets(ctx, nsys, offsets, as_stream(stream), off));
     const int64_t total = off[nsys];
     if (total == 0) return NB_OK;
+    if (steps > (1 << 20)) return fail(ctx, NB_ERR_INVALID, "at most 2^20 steps per batched call");
     NB_TRY(check_ptr(ctx, x, 4, "x", nullptr));
     NB_TRY(check_ptr(ctx, v, 4, "v", nullptr));
     NB_TRY(check_ptr(ctx, m, 4, "m", nullptr));
@@ -1010,7 +1011,6 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
         plan.nt = tuned->second.nt;
         plan.r = tuned->second.r;
         plan.jt = tuned->second.jt;
-        plan.gmax = tuned->second.gmax;
     }
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
@@ -1066,32 +1066,29 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     BatchPlan best;
     for (int r : {1, 2, 4}) {
         for (int jt : {64, 128}) {
-            for (int gmax : {8, 16}) {
-                BatchPlan plan;
-                plan.r = r;
-                plan.jt = jt;
-                plan.gmax = gmax;
-                std::string why;
-                if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
-                NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
-                NB_CUDA(batched_upload(plan, ctx->bat.p, st));
-                float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
-                NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
-                const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
-                NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, eps2, (float)ctx->p.G,
-                                        (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
-                NB_CUDA(cudaEventRecord(e0, st));
-                NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, eps2, (float)ctx->p.G,
-                                        (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
-                NB_CUDA(cudaEventRecord(e1, st));
-                NB_CUDA(cudaEventSynchronize(e1));
-                ctx->launches += 6;
-                float ms = 0.f;
-                NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = plan;
-                }
+            BatchPlan plan;
+            plan.r = r;
+            plan.jt = jt;
+            std::string why;
+            if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
+            NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
+            NB_CUDA(batched_upload(plan, ctx->bat.p, st));
+            float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
+            NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
+            const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, eps2, (float)ctx->p.G,
+                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(cudaEventRecord(e0, st));
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, eps2, (float)ctx->p.G,
+                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(cudaEventRecord(e1, st));
+            NB_CUDA(cudaEventSynchronize(e1));
+            ctx->launches += 6;
+            float ms = 0.f;
+            NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = plan;
             }
         }
     }
@@ -1116,7 +1113,6 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     if (from_tune) {
         plan.r = tuned->second.r;
         plan.jt = tuned->second.jt;
-        plan.gmax = tuned->second.gmax;
     }
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
@@ -1124,7 +1120,7 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     out6[0] = plan.nt;
     out6[1] = plan.r;
     out6[2] = plan.jt;
-    out6[3] = plan.gmax;
+    out6[3] = plan.items_per_step;
     out6[4] = plan.ncta;
     out6[5] = from_tune ? 1 : 0;
     return NB_OK;

@@ -1,11 +1,14 @@
 // Persistent ensemble kernel: every system of the batch advances `steps`
-// paper steps inside one cooperative launch. CTAs are grouped in gangs; a
-// gang walks its list of systems, and for each step every member computes the
-// forces on its slice of i-bodies from all j-bodies of the system (j-tiles
-// streamed by 1-D bulk copies, issued by thread 0, through a shared-memory
-// ring as in the single-system kernel), applies the half kick and the drift,
-// writes the repacked positions to the other buffer and meets the rest of the
-// gang at a bounded global-memory barrier before the next step.
+// paper steps inside one cooperative launch, as a dataflow over work items
+// (system, step, i-chunk). Persistent CTAs pop items from one atomic queue in
+// step-major order (largest systems first within a step); an item waits,
+// bounded, until every item of the previous step of its own system is done,
+// then computes the forces on its i-chunk from all j-bodies of the system
+// (j-tiles streamed by 1-D bulk copies, issued by thread 0, through a
+// shared-memory ring as in the single-system kernel), applies the half kick
+// and the drift, writes the repacked positions to the other buffer and
+// releases itself. The oldest unfinished item never waits, so the queue
+// always makes progress, and load balance is within one item.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,11 +25,12 @@ namespace {
 
 struct BatchArgs {
     const int64_t *off, *poff;
-    const int *work, *gang_first, *cta_gang, *cta_rank, *gang_size;
-    unsigned *gang_ctr;
+    const int *item_sys, *item_chunk, *nchunks;
+    unsigned *next;  // queue head
+    unsigned *done;  // [nsys] items completed, cumulative over steps
     float4 *xm0, *xm1;
     float *x, *v;
-    int steps, jt;
+    int steps, jt, items_per_step;
     float eps2, G, dt;
     int *err;
     uint64_t timeout_ns;
@@ -42,27 +46,22 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// All gang members reach the barrier `epoch` times before anyone passes it
-// the epoch-th time. The wait is bounded; on timeout an error bit is set and
-// the CTA goes on (its results are then flagged invalid by the host).
-__device__ void gang_barrier(unsigned *ctr, unsigned target, uint64_t timeout_ns, int *err) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        if (ld_acquire(ctr) < target) {
-            const uint64_t t0 = global_ns();
-            while (ld_acquire(ctr) < target) {
-                __nanosleep(64);
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicOr(err, kErrGang);
-                    break;
-                }
-            }
-        }
-        __threadfence();
+// Pair-layout scalar read through L2 only: another CTA may have written it
+// earlier in this launch, and a line this SM cached before must not be used.
+__device__ __forceinline__ float pair_get_cg(const float4 *base, int64_t i, int c) {
+    const float *p = reinterpret_cast<const float *>(base + (i >> 1) * 2);
+    return __ldcg(p + 2 * c + (int)(i & 1));
+}
+
+// Bounded wait until *p >= target; false on timeout.
+__device__ bool wait_at_least(const unsigned *p, unsigned target, uint64_t timeout_ns) {
+    if (ld_acquire(p) >= target) return true;
+    const uint64_t t0 = global_ns();
+    while (ld_acquire(p) < target) {
+        __nanosleep(64);
+        if (global_ns() - t0 > timeout_ns) return false;
     }
-    __syncthreads();
+    return true;
 }
 
 template <int NT, int R>
@@ -71,15 +70,14 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + kStages;
     float4 *ring = reinterpret_cast<float4 *>(smem_raw + 128);
+    __shared__ unsigned s_item;
+    __shared__ int s_abort;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int gang = a.cta_gang[blockIdx.x];
-    const int rank = a.cta_rank[blockIdx.x];
-    const int gsz = a.gang_size[gang];
-    unsigned *ctr = a.gang_ctr + gang;
     const int f4_per_tile = a.jt;  // (jt / 2) records x 2 float4
     const uint32_t tile_bytes = (uint32_t)f4_per_tile * 16u;
     const float dt = a.dt;
+    const unsigned total = (unsigned)a.items_per_step * (unsigned)a.steps;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -91,12 +89,11 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     __syncthreads();
 
     // Ring position q (tiles streamed so far by this CTA) runs on across
-    // passes, steps and systems; slot q % kStages, phase q / kStages. Thread 0
-    // issues position q once position q - kStages has been released.
-    uint32_t kk = 0;       // position of the current pass's first tile
+    // items; slot q % kStages, phase q / kStages. Thread 0 issues position q
+    // once position q - kStages has been released by every warp.
+    uint32_t kk = 0;       // position of the current item's first tile
     uint32_t issued = 0;   // positions issued so far (thread 0)
-    unsigned epoch = 0;    // gang barriers passed
-    bool give_up = false;  // a wait failed: stop streaming, keep the barriers
+    bool give_up = false;  // a ring wait failed: stop streaming
 
     auto issue = [&](uint32_t q, const float4 *src_tile) {
         const int slot = q % kStages;
@@ -111,89 +108,102 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
         issued = q + 1;
     };
 
-    for (int w = a.gang_first[gang]; w < a.gang_first[gang + 1]; ++w) {
-        const int s = a.work[w];
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(a.next, 1u);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const unsigned id = s_item;
+        if (id >= total) break;
+        const int t = (int)(id / (unsigned)a.items_per_step);
+        const int k = (int)(id % (unsigned)a.items_per_step);
+        const int s = a.item_sys[k];
+        const int c = a.item_chunk[k];
         const int64_t b0 = a.off[s];
         const int64_t n = a.off[s + 1] - b0;
         const int64_t p0 = a.poff[s];
-        const int64_t npad = (n + a.jt - 1) / a.jt * a.jt;
-        const int ntl = (int)(npad / a.jt);
-        const int64_t chunk = (n + gsz - 1) / gsz;
-        const int64_t lo = (int64_t)rank * chunk;
-        const int64_t hi = lo + chunk < n ? lo + chunk : n;
-        const int passes = hi > lo ? (int)((hi - lo + (int64_t)NT * R - 1) / ((int64_t)NT * R)) : 0;
-        for (int t = 0; t < a.steps; ++t) {
-            const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
-            float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
-            if (tid == 0) fence_proxy_async_global();
-            for (int ps = 0; ps < passes; ++ps) {
-                if (tid == 0 && !give_up)
-                    for (int k = 0; k < ntl && k < kStages - 1 && !give_up; ++k)
-                        issue(kk + k, src + (int64_t)k * f4_per_tile);
-                const int64_t ibase = lo + (int64_t)ps * NT * R;
-                AccelF32x2::I ist[R];
-                AccelF32x2::T tot[R];
-                AccelF32x2::C cst;
-                cst.eps2 = dup(a.eps2);
+        const int ntl = (int)((n + a.jt - 1) / a.jt);
+        const int64_t lo = (int64_t)c * NT * R;
+        const int64_t hi = lo + (int64_t)NT * R < n ? lo + (int64_t)NT * R : n;
+        const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
+        float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
+        if (tid == 0) {
+            // step t of system s needs every item of its step t-1
+            if (t > 0 && !wait_at_least(a.done + s, (unsigned)t * (unsigned)a.nchunks[s], a.timeout_ns)) {
+                atomicOr(a.err, kErrGang);
+                s_abort = 1;
+            }
+            fence_proxy_async_global();
+        }
+        __syncthreads();
+        const bool run = !s_abort && !give_up;
+        if (tid == 0 && run)
+            for (int q = 0; q < ntl && q < kStages - 1 && !give_up; ++q)
+                issue(kk + q, src + (int64_t)q * f4_per_tile);
+        AccelF32x2::I ist[R];
+        AccelF32x2::T tot[R];
+        AccelF32x2::C cst;
+        cst.eps2 = dup(a.eps2);
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    int64_t i = ibase + r * NT + tid;
-                    if (i >= hi) i = lo;
-                    ist[r].nx = dup(-pair_get(src, i, 0));
-                    ist[r].ny = dup(-pair_get(src, i, 1));
-                    ist[r].nz = dup(-pair_get(src, i, 2));
-                    AccelF32x2::zero_total(tot[r]);
+        for (int r = 0; r < R; ++r) {
+            int64_t i = lo + r * NT + tid;
+            if (i >= hi) i = lo;
+            ist[r].nx = dup(-pair_get_cg(src, i, 0));
+            ist[r].ny = dup(-pair_get_cg(src, i, 1));
+            ist[r].nz = dup(-pair_get_cg(src, i, 2));
+            AccelF32x2::zero_total(tot[r]);
+        }
+        if (run) {
+            for (int q = 0; q < ntl; ++q) {
+                const uint32_t pos = kk + q;
+                const int slot = pos % kStages;
+                if (!give_up && !mbar_wait(&full[slot], (pos / kStages) & 1, a.timeout_ns)) {
+                    atomicOr(a.err, kErrFullWait);
+                    give_up = true;
                 }
-                for (int k = 0; k < ntl; ++k) {
-                    const uint32_t q = kk + k;
-                    const int slot = q % kStages;
-                    if (!give_up && !mbar_wait(&full[slot], (q / kStages) & 1, a.timeout_ns)) {
-                        atomicOr(a.err, kErrFullWait);
-                        give_up = true;
-                    }
-                    if (!give_up) {
-                        const float4 *tile = ring + slot * f4_per_tile;
+                if (!give_up) {
+                    const float4 *tile = ring + slot * f4_per_tile;
 #pragma unroll 2
-                        for (int jp = 0; jp < (a.jt >> 1); ++jp) {
-                            float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
+                    for (int jp = 0; jp < (a.jt >> 1); ++jp) {
+                        float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
 #pragma unroll
-                            for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
-                        }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
                     }
-                    // refill: position q + kStages - 1 goes into the slot of q - 1
-                    if (tid == 0 && !give_up && k + kStages - 1 < ntl)
-                        issue(q + kStages - 1, src + (int64_t)(k + kStages - 1) * f4_per_tile);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[slot]);
                 }
-                kk += ntl;
+                // refill: position pos + kStages - 1 goes into the slot of pos - 1
+                if (tid == 0 && !give_up && q + kStages - 1 < ntl)
+                    issue(pos + kStages - 1, src + (int64_t)(q + kStages - 1) * f4_per_tile);
+            }
+            kk += ntl;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int64_t i = ibase + r * NT + tid;
-                    if (i < hi) {
-                        const float ax = a.G * (tot[r].x.x + tot[r].x.y);
-                        const float ay = a.G * (tot[r].y.x + tot[r].y.y);
-                        const float az = a.G * (tot[r].z.x + tot[r].z.y);
-                        float *xp = a.x + 3 * (b0 + i);
-                        float *vp = a.v + 3 * (b0 + i);
-                        const float acc[3] = {ax, ay, az};
-                        float xs[3];
+            for (int r = 0; r < R; ++r) {
+                const int64_t i = lo + r * NT + tid;
+                if (i < hi) {
+                    const float acc[3] = {a.G * (tot[r].x.x + tot[r].x.y), a.G * (tot[r].y.x + tot[r].y.y),
+                                          a.G * (tot[r].z.x + tot[r].z.y)};
+                    float *xp = a.x + 3 * (b0 + i);
+                    float *vp = a.v + 3 * (b0 + i);
+                    float xs[3];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            // v += a dt/2 (the printed half kick); x += v dt
-                            float vc = __fadd_rn(vp[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
-                            vp[c] = vc;
-                            xs[c] = __fadd_rn(xp[c], __fmul_rn(vc, dt));
-                            xp[c] = xs[c];
-                        }
-                        pair_put(dst, i, xs[0], xs[1], xs[2], pair_get(src, i, 3));
+                    for (int cc = 0; cc < 3; ++cc) {
+                        // v += a dt/2 (the printed half kick); x += v dt
+                        const float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                        vp[cc] = vc;
+                        xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
+                        xp[cc] = xs[cc];
                     }
+                    pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
                 }
             }
-            // the whole system moves before anyone reads the next positions
             fence_proxy_async_global();
-            ++epoch;
-            gang_barrier(ctr, epoch * (unsigned)gsz, a.timeout_ns, a.err);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.done + s, 1u);  // release this item to step t+1
         }
     }
     // never leave while our own copies may still be landing
@@ -244,7 +254,7 @@ size_t batched_smem(int jt) {
 
 // Device copy of the plan inside the scratch block.
 struct Layout {
-    size_t o_off, o_poff, o_work, o_gf, o_cg, o_cr, o_gs, o_ctr, o_xm0, o_xm1, total;
+    size_t o_off, o_poff, o_isys, o_ichunk, o_nch, o_next, o_done, o_xm0, o_xm1, total;
 };
 
 Layout layout_of(const BatchPlan &p) {
@@ -257,37 +267,15 @@ Layout layout_of(const BatchPlan &p) {
     };
     L.o_off = take(p.off.size() * 8);
     L.o_poff = take(p.poff.size() * 8);
-    L.o_work = take(p.work.size() * 4);
-    L.o_gf = take(p.gang_first.size() * 4);
-    L.o_cg = take(p.cta_gang.size() * 4);
-    L.o_cr = take(p.cta_rank.size() * 4);
-    L.o_gs = take(p.gang_size.size() * 4);
-    L.o_ctr = take((size_t)p.ngang * 4);
+    L.o_isys = take(p.item_sys.size() * 4);
+    L.o_ichunk = take(p.item_chunk.size() * 4);
+    L.o_nch = take(p.nchunks.size() * 4);
+    L.o_next = take(4);                            // queue head ...
+    L.o_done = take((size_t)p.nsys * 4);          // ... and completion counters: zeroed per launch
     L.o_xm0 = take((size_t)p.total_pad * 16);
     L.o_xm1 = take((size_t)p.total_pad * 16);
     L.total = o;
     return L;
-}
-
-// per-CTA time of system (n) on a gang of g CTAs, in tile-pass units
-double sys_time(int64_t n, int g, int nt, int r, int jt) {
-    const int64_t chunk = (n + g - 1) / g;
-    const int64_t passes = (chunk + (int64_t)nt * r - 1) / ((int64_t)nt * r);
-    const int64_t ntl = (n + jt - 1) / jt;
-    const double beta = 6.0;  // per-step latency: ring fill, epilogue, barrier
-    return (double)passes * ntl + beta;
-}
-
-// Longest-processing-time-first packing of `items` (time, id) onto k bins.
-double lpt(const std::vector<std::pair<double, int>> &items, int k, std::vector<int> *assign) {
-    std::vector<double> load(k, 0.0);
-    if (assign) assign->assign(items.size(), 0);
-    for (size_t q = 0; q < items.size(); ++q) {
-        int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        load[b] += items[q].first;
-        if (assign) (*assign)[q] = b;
-    }
-    return *std::max_element(load.begin(), load.end());
 }
 
 }  // namespace
@@ -296,6 +284,7 @@ int64_t batched_max_n() { return int64_t(1) << 20; }
 
 bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, BatchPlan &p,
                   std::string &why) {
+    (void)device;
     p.nsys = (int)off.size() - 1;
     if (p.nt == 0) p.nt = 128;
     if (p.r == 0) p.r = 2;
@@ -317,108 +306,35 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
         why = "occupancy query failed";
         return false;
     }
-    (void)device;
-    const int P = occ * num_sms;
     p.off = off;
     p.poff.assign(p.nsys, 0);
+    p.nchunks.assign(p.nsys, 0);
     p.total = off[p.nsys];
+    const int64_t chunk = (int64_t)p.nt * p.r;
     int64_t acc = 0;
     for (int s = 0; s < p.nsys; ++s) {
+        const int64_t n = off[s + 1] - off[s];
         p.poff[s] = acc;
-        acc += (off[s + 1] - off[s] + p.jt - 1) / p.jt * p.jt;
+        acc += (n + p.jt - 1) / p.jt * p.jt;
+        p.nchunks[s] = (int)((n + chunk - 1) / chunk);
     }
     p.total_pad = std::max<int64_t>(acc, p.jt);
-
-    // gang sizes and LPT assignment under a makespan bound T (bisection)
-    const int gmax = std::max(1, std::min(p.gmax > 0 ? p.gmax : 16, P));
-    std::vector<int> sizes;
-    for (int g = 1; g <= gmax; g *= 2) sizes.push_back(g);
-    double lb = 0.0, work = 0.0;
-    for (int s = 0; s < p.nsys; ++s) {
-        const int64_t n = off[s + 1] - off[s];
-        if (n == 0) continue;
-        work += sys_time(n, 1, p.nt, p.r, p.jt);
-        lb = std::max(lb, sys_time(n, gmax, p.nt, p.r, p.jt));
-    }
-    lb = std::max(lb, work / P);
-    std::map<int, std::vector<std::pair<double, int>>> groups;
-    std::map<int, int> kg;
-    auto feasible = [&](double T, bool commit) -> bool {
-        std::map<int, std::vector<std::pair<double, int>>> gr;
-        for (int s = 0; s < p.nsys; ++s) {
-            const int64_t n = off[s + 1] - off[s];
-            if (n == 0) continue;
-            int gs = gmax;
-            for (int g : sizes)
-                if (sys_time(n, g, p.nt, p.r, p.jt) <= T) { gs = g; break; }
-            gr[gs].push_back({sys_time(n, gs, p.nt, p.r, p.jt), s});
+    // items of one step: largest systems first, chunks in order
+    std::vector<int> order(p.nsys);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return off[a + 1] - off[a] > off[b + 1] - off[b];
+    });
+    p.item_sys.clear();
+    p.item_chunk.clear();
+    for (int s : order)
+        for (int c = 0; c < p.nchunks[s]; ++c) {
+            p.item_sys.push_back(s);
+            p.item_chunk.push_back(c);
         }
-        int used = 0;
-        std::map<int, int> kk;
-        for (auto &kv : gr) {
-            auto &items = kv.second;
-            std::sort(items.begin(), items.end(), [](auto &A, auto &B) {
-                return A.first > B.first || (A.first == B.first && A.second < B.second);
-            });
-            double tot = 0;
-            for (auto &it : items) tot += it.first;
-            int k = std::max(1, (int)std::ceil(tot / T));
-            while (k < (int)items.size() && lpt(items, k, nullptr) > T) ++k;
-            k = std::min<int>(k, (int)items.size());
-            kk[kv.first] = k;
-            used += k * kv.first;
-        }
-        if (used > P) return false;
-        if (commit) {
-            groups = gr;
-            kg = kk;
-        }
-        return true;
-    };
-    double lo = lb, hi = lb;
-    while (!feasible(hi, false)) {
-        hi *= 1.5;
-        if (hi > 1e15) { why = "no feasible schedule"; return false; }
-    }
-    for (int it = 0; it < 40; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (feasible(mid, false)) hi = mid; else lo = mid;
-    }
-    feasible(hi, true);
-    p.makespan_tiles = hi;
-
-    p.work.clear();
-    p.gang_first.assign(1, 0);
-    p.cta_gang.clear();
-    p.cta_rank.clear();
-    p.gang_size.clear();
-    for (auto &kv : groups) {
-        const int g = kv.first;
-        const int k = kg[g];
-        std::vector<int> assign;
-        lpt(kv.second, k, &assign);
-        for (int b = 0; b < k; ++b) {
-            const int gang = (int)p.gang_size.size();
-            p.gang_size.push_back(g);
-            for (size_t q = 0; q < kv.second.size(); ++q)
-                if (assign[q] == b) p.work.push_back(kv.second[q].second);
-            p.gang_first.push_back((int)p.work.size());
-            for (int rnk = 0; rnk < g; ++rnk) {
-                p.cta_gang.push_back(gang);
-                p.cta_rank.push_back(rnk);
-            }
-        }
-    }
-    if (p.work.empty()) {  // only empty systems: one idle gang
-        p.gang_size.push_back(1);
-        p.gang_first.push_back(0);
-        p.cta_gang.push_back(0);
-        p.cta_rank.push_back(0);
-    }
-    p.ngang = (int)p.gang_size.size();
-    p.ncta = (int)p.cta_gang.size();
+    p.items_per_step = (int)p.item_sys.size();
+    p.ncta = std::max(1, std::min(occ * num_sms, std::max(p.items_per_step, 1)));
     Layout L = layout_of(p);
-    p.plan_bytes = L.o_ctr;
     p.scratch_bytes = L.total;
     // signature: FNV-1a over sizes and shape
     uint64_t h = 1469598103934665603ull;
@@ -433,7 +349,6 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
     mix((uint64_t)p.r);
     mix((uint64_t)p.jt);
     mix((uint64_t)p.ncta);
-    mix((uint64_t)p.gmax);
     p.signature = h;
     return true;
 }
@@ -443,16 +358,16 @@ cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
     char *b = (char *)scratch;
     cudaError_t e;
 #define NB_UP(field, o)                                                                      \
-    e = cudaMemcpyAsync(b + (o), p.field.data(), p.field.size() * sizeof(p.field[0]),       \
-                        cudaMemcpyHostToDevice, st);                                         \
-    if (e != cudaSuccess) return e;
+    if (!p.field.empty()) {                                                                  \
+        e = cudaMemcpyAsync(b + (o), p.field.data(), p.field.size() * sizeof(p.field[0]),   \
+                            cudaMemcpyHostToDevice, st);                                     \
+        if (e != cudaSuccess) return e;                                                      \
+    }
     NB_UP(off, L.o_off)
     NB_UP(poff, L.o_poff)
-    NB_UP(work, L.o_work)
-    NB_UP(gang_first, L.o_gf)
-    NB_UP(cta_gang, L.o_cg)
-    NB_UP(cta_rank, L.o_cr)
-    NB_UP(gang_size, L.o_gs)
+    NB_UP(item_sys, L.o_isys)
+    NB_UP(item_chunk, L.o_ichunk)
+    NB_UP(nchunks, L.o_nch)
 #undef NB_UP
     return cudaSuccess;
 }
@@ -468,29 +383,31 @@ cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, float *x, 
 cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *v, const float *m,
                             int steps, float eps2, float G, float dt, int *err,
                             uint64_t timeout_ns, cudaStream_t st) {
+    if ((uint64_t)p.items_per_step * (uint64_t)steps + (uint64_t)p.ncta >= (1ull << 32))
+        return cudaErrorInvalidValue;
     Layout L = layout_of(p);
     char *b = (char *)scratch;
     BatchArgs a;
     a.off = (const int64_t *)(b + L.o_off);
     a.poff = (const int64_t *)(b + L.o_poff);
-    a.work = (const int *)(b + L.o_work);
-    a.gang_first = (const int *)(b + L.o_gf);
-    a.cta_gang = (const int *)(b + L.o_cg);
-    a.cta_rank = (const int *)(b + L.o_cr);
-    a.gang_size = (const int *)(b + L.o_gs);
-    a.gang_ctr = (unsigned *)(b + L.o_ctr);
+    a.item_sys = (const int *)(b + L.o_isys);
+    a.item_chunk = (const int *)(b + L.o_ichunk);
+    a.nchunks = (const int *)(b + L.o_nch);
+    a.next = (unsigned *)(b + L.o_next);
+    a.done = (unsigned *)(b + L.o_done);
     a.xm0 = (float4 *)(b + L.o_xm0);
     a.xm1 = (float4 *)(b + L.o_xm1);
     a.x = x;
     a.v = v;
     a.steps = steps;
     a.jt = p.jt;
+    a.items_per_step = p.items_per_step;
     a.eps2 = eps2;
     a.G = G;
     a.dt = dt;
     a.err = err;
     a.timeout_ns = timeout_ns;
-    cudaError_t e = cudaMemsetAsync(a.gang_ctr, 0, (size_t)p.ngang * 4, st);
+    cudaError_t e = cudaMemsetAsync(b + L.o_next, 0, L.o_xm0 - L.o_next, st);
     if (e != cudaSuccess) return e;
     batched_pack_kernel<<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, x, m, a.xm0);
     e = cudaGetLastError();

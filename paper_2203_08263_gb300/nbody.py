@@ -201,7 +201,7 @@ class Context:
         out = (_i * 6)()
         self._check(self.lib.nb_get_batched_config(self.h, int(offsets.shape[0]) - 1, _ptr(offsets), out),
                     "nb_get_batched_config")
-        return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "gang_max": out[3],
+        return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "items_per_step": out[3],
                 "ctas": out[4], "tuned": bool(out[5])}
 
     # ---- reverse
