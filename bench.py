@@ -170,6 +170,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per launch of the step kernel (force sum + kick/drift epilogue)
+# at N = 262144, by launch shape (threads, bodies/thread, j-split, j-tile):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch each, on this
+# GPU type. Most of it is split partials evicted from L2; the O(N) state is
+# 21 MB. Reported only when the bench runs one of these shapes.
+STEP_TRAFFIC_BYTES = {
+    (128, 4, 16, 256): 11.16e6 + 21.29e6,
+    (128, 8, 19, 256): 11.77e6 + 34.34e6,
+    (128, 8, 26, 256): 12.73e6 + 63.50e6,
+    (256, 2, 16, 256): 10.96e6 + 21.27e6,
+}
+
+
 def fp32_peak_tflops(props, sm_max_mhz):
     # 128 FP32 lanes per SM, 2 flops per FMA, at the maximum SM clock
     return props.multi_processor_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
@@ -237,8 +250,10 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = fp32_peak_tflops(props, sm_max)
     achieved = FLOPS_PER_INTERACTION * inter / (ms_step / 1e3) / 1e12
+    shape_key = (cfg["threads"], cfg["bodies_per_thread"], cfg["split"], cfg["jtile"])
+    traffic = STEP_TRAFFIC_BYTES.get(shape_key) if n == 262144 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                               "(max SM clock); 20 flops per interaction",
                 "kernel": "force_kernel<AccelF32x2> (+ its 1-launch pack, <0.1% of the step)"}
@@ -309,7 +324,7 @@ def extras(ctx0, torch, dev, np):
     c = Context(1.0, 0.01, 1e-3, device=dev.index)
     x, v, m = (torch.tensor(a, dtype=torch.float32, device=dev) for a in (s.x, s.v, s.m))
     c.run(x.clone(), v.clone(), m, 10)
-    t = min(_timed(torch, lambda: c.run(x, v, m, 10)) for _ in range(5))
+    t = min(_timed(torch, dev, lambda: c.run(x, v, m, 10)) for _ in range(5))
     out["c1_small"] = {"n": 1024, "steps": 10, "s": t, "us_per_step": t / 10 * 1e6,
                        "interactions_per_s": 1024.0 * 1024 * 10 / t, "shape": c.get_config(1024)}
     c.close()

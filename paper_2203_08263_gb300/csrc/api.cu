@@ -482,7 +482,7 @@ nb_status sync_and_check(nb_ctx *ctx, cudaStream_t st) {
         NB_CUDA(cudaMemset(ctx->err_word, 0, sizeof(int)));
         return fail(ctx, NB_ERR_TIMEOUT,
                     "device-side wait gave up (error bits 0x%x: 1 tile wait, 2 slot wait, "
-                    "4 copy drain, 8 gang barrier); results of the affected calls are invalid",
+                    "4 copy drain, 8 batched step dependency); results of the affected calls are invalid",
                     h);
     }
     return NB_OK;

@@ -108,9 +108,14 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
         issued = q + 1;
     };
 
+    // Thread 0 takes the next item number one item ahead, so the queue's
+    // atomic latency overlaps the current item. Holding one unstarted item
+    // cannot stall the queue: the lowest unfinished item is always one that
+    // some CTA is running, and its dependencies are all finished.
+    unsigned next_id = tid == 0 ? atomicAdd(a.next, 1u) : 0u;
     for (;;) {
         if (tid == 0) {
-            s_item = atomicAdd(a.next, 1u);
+            s_item = next_id;
             s_abort = 0;
         }
         __syncthreads();
@@ -135,6 +140,7 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
                 s_abort = 1;
             }
             fence_proxy_async_global();
+            next_id = atomicAdd(a.next, 1u);
         }
         __syncthreads();
         const bool run = !s_abort && !give_up;

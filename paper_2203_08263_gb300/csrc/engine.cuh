@@ -45,7 +45,7 @@ enum ErrBits : int {
     kErrFullWait = 1,   // consumer gave up waiting for a tile
     kErrEmptyWait = 2,  // producer gave up waiting for a free slot
     kErrDrain = 4,      // producer gave up waiting for its own copies
-    kErrGang = 8,       // batched kernel: gang barrier gave up
+    kErrGang = 8,       // batched kernel: wait for a previous step gave up
 };
 
 enum DebugBits : int {
