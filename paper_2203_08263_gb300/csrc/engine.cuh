@@ -36,6 +36,10 @@ namespace nb {
 #define NB_PRODUCER_WARP 0  // 0: consumer thread 0 issues the copies; 1: a dedicated warp does
 #endif
 
+#ifndef NB_COMP_NEWTON
+#define NB_COMP_NEWTON 1  // Newton step on the MUFU rsqrt in the precision-form forces
+#endif
+
 constexpr int kStages = 4;        // ring depth
 constexpr int kProducerThreads = NB_PRODUCER_WARP ? 32 : 0;
 constexpr int kPadBodies = 256;   // packed arrays hold a multiple of this
@@ -682,9 +686,11 @@ struct AccelComp {
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
         float2 y = rsqrt_mufu2(q);
+#if NB_COMP_NEWTON
         // one Newton step for q^(-1/2): y <- y (3/2 - q y^2 / 2)
         const float2 tq = __fmul2_rn(__fmul2_rn(q, c.mhalf), y);
         y = __fmul2_rn(y, __ffma2_rn(tq, y, c.three_half));
+#endif
         const float2 y2 = __fmul2_rn(y, y);
         float2 w = __fmul2_rn(f2(rec[1].z, rec[1].w), y);
         w = __fmul2_rn(w, y2);
