@@ -183,6 +183,9 @@ STEP_TRAFFIC_BYTES = {
 }
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # unit counts x maximum SM clock
+
+
 def fp32_peak_tflops(props, sm_max_mhz):
     # 128 FP32 lanes per SM, 2 flops per FMA, at the maximum SM clock
     return props.multi_processor_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
@@ -343,6 +346,12 @@ def extras(ctx0, torch, dev, np):
     out["c3_precision_form"] = {"n": n, "steps": 2, "interactions_per_s": 2 * float(n) * n / t,
                                 "accel_rel_l2_vs_fp64_oracle_256_subset": float(err), "s": t,
                                 "shape": c.get_config(n)}
+    # diagnostics on the C3 state: P, KE, softened potential (O(N^2)), H'
+    t0 = time.perf_counter()
+    e = c.energy(x, v, m)
+    te = time.perf_counter() - t0
+    out["c3_diagnostics"] = {"n": n, "s": te, "pairs_per_s": float(n) * n / te, "KE": e["KE"],
+                             "Phi": e["Phi"], "H": e["H"], "P": [float(p_) for p_ in e["P"]]}
     c.close()
     del x, v, m, a
     # C4: batched ensemble, 512 systems, 100 steps, one persistent launch
@@ -381,7 +390,47 @@ def extras(ctx0, torch, dev, np):
     out["c5_adjoint"] = {"n": n, "T": T, "k": k, "forward_s": tf, "backward_s": tb, "ratio": tb / tf,
                          "forward_interactions_per_s": float(n) * n * T / tf}
     c.close()
+    out["cpu_oracle_rows"] = oracle_rows()
+    out["fp32_peak_fraction"] = {
+        k: FLOPS_PER_INTERACTION * out[k]["interactions_per_s"] / 1e12 / FP32_PEAK_TFLOPS
+        for k in ("c1_small", "c3_precision_form", "c4_batched")}
     return out
+
+
+def oracle_rows():
+    """The FP64 oracle, as it stands, on bounded samples of the other rows
+    (host cores of this machine), for comparison with the GPU rates above."""
+    import numpy as np
+
+    import oracle
+    from paper_2203_08263_gb300 import ics
+
+    rows = {}
+    s = ics.plummer(1 << 20, seed=2)
+    idx = ics.subset_indices(1 << 20, 512, 5)
+    t0 = time.perf_counter()
+    oracle.accel(s.x, s.m, 1.0, 0.05, idx)
+    dt = time.perf_counter() - t0
+    rows["c3_accel"] = {"interactions_per_s": 512.0 * (1 << 20) / dt, "sample": "512 i x 2^20 j"}
+    off, x, v, m = ics.ensemble(512, 3)
+    pick = np.argsort(np.diff(off))[-4:]
+    t0 = time.perf_counter()
+    inter = 0.0
+    for sys_ in pick:
+        a, b = off[sys_], off[sys_ + 1]
+        oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 2)
+        inter += 2.0 * (b - a) ** 2
+    dt = time.perf_counter() - t0
+    rows["c4_systems"] = {"interactions_per_s": inter / dt, "sample": "2 steps of the 4 largest systems"}
+    n, T = 512, 20
+    s = ics.cube(n, seed=4, masses="equal")
+    t0 = time.perf_counter()
+    oracle.adjoint(s.x, s.v, s.m, 1.0, 0.01, 1e-3, T, np.ones((n, 3)), np.zeros((n, 3)))
+    dt = time.perf_counter() - t0
+    rows["c5_adjoint"] = {"s": dt, "forward_interactions_per_s": float(n) * n * T / dt,
+                          "sample": f"full adjoint (forward + reverse, explicit Jacobian blocks), N={n}, T={T}"}
+    rows["cores"] = oracle.num_threads()
+    return rows
 
 
 def main():

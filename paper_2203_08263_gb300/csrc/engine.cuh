@@ -37,7 +37,11 @@ namespace nb {
 #endif
 
 #ifndef NB_COMP_NEWTON
-#define NB_COMP_NEWTON 1  // Newton step on the MUFU rsqrt in the precision-form forces
+// 1: one FP32 Newton step on the MUFU rsqrt in the precision-form kernels.
+// Off by default: measured on the 2^20-body Plummer sphere it raises the
+// force error (4.5e-8 vs 2.7e-8 relative L2; an FP32 Newton step cannot beat
+// FP32 rounding and adds its own) and costs 4 FP32 ops per interaction.
+#define NB_COMP_NEWTON 0
 #endif
 
 constexpr int kStages = 4;        // ring depth
@@ -654,10 +658,10 @@ struct AccelMath {
     __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) { AccelScalar::finish(a, i, f); }
 };
 
-// Precision form: FP32 pair terms with one Newton-Raphson refinement of the
-// MUFU reciprocal square root (y <- y (3/2 - s y^2 / 2)), plain FP32 sums
-// within a j-tile, and the per-tile sums folded into a (hi, lo) pair with
-// Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
+// Precision form: FP32 pair terms (optionally one Newton-Raphson refinement
+// of the MUFU reciprocal square root, y <- y (3/2 - s y^2 / 2), see
+// NB_COMP_NEWTON), plain FP32 sums within a j-tile, and the per-tile sums
+// folded into a (hi, lo) pair with Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
 // update run in FP64.
 struct AccelComp {
     static constexpr bool SELF_MASK = false;
@@ -887,7 +891,7 @@ struct VjpF32x2 {
 // Precision form of the VJP. Positions enter as FP32 (hi, lo) pairs of the
 // FP64 state, and d = (x_j^hi - x_k^hi) + (x_j^lo - x_k^lo) keeps its
 // relative error at FP32 rounding even for close pairs (whose terms weigh
-// as |d|^-3); the rsqrt gets one Newton step; sums are FP32 within a tile
+// as |d|^-3); the rsqrt is refined only with NB_COMP_NEWTON; sums are FP32 within a tile
 // and two-summed (hi, lo) across tiles; the epilogue runs in FP64 with FP64
 // m_k and abar_k. Records, 5 float4 per pair of bodies:
 //   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,xl0,xl1} {yl0,yl1,zl0,zl1}
@@ -943,8 +947,10 @@ struct VjpComp {
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
         float2 y = rsqrt_mufu2(q);
+#if NB_COMP_NEWTON
         const float2 tq = __fmul2_rn(__fmul2_rn(q, c.mhalf), y);
         y = __fmul2_rn(y, __ffma2_rn(tq, y, c.three_half));
+#endif
         if constexpr (MASK) y = __fmul2_rn(y, keep);
         VjpF32x2::terms(dx, dy, dz, y, f2(rec[1].z, rec[1].w), f2(rec[2].x, rec[2].y),
                         f2(rec[2].z, rec[2].w), f2(rec[3].x, rec[3].y), s.b, t);
