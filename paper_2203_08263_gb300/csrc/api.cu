@@ -268,8 +268,8 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n) {
     } else if (pol == kPolPot) {
         r = 2;
         if (n >= 4096) jt = 128;
-    } else {  // VJP
-        r = n >= 8192 ? 2 : 1;
+    } else {  // VJP (the precision form's R = 2 instance spills at the 128-register cap)
+        r = (n >= 8192 && pol == kPolVjp) ? 2 : 1;
         if (n >= 4096) jt = 128;
     }
     return finish_shape(ctx, pol, nt, r, jt, 0, n);

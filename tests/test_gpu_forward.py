@@ -238,3 +238,29 @@ def test_energy_diagnostics(nbm, prec):
     # H' = KE + Phi/2 nearly cancels for a virialised sphere: bound it by the
     # size of its two terms
     assert abs(e["H"] - r["H"]) <= 1e-6 * (abs(r["KE"]) + 0.5 * abs(r["Phi"]))
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_denominator_ablation_variants_match_oracle(nbm, variant):
+    """The sqrt-then-divide and powf denominators (the paper's math-operation
+    experiment) compute the same forces."""
+    n, G, eps = 3001, 1.0, 0.02
+    s = ics.cube(n, seed=70 + variant)
+    ctx = nbm.Context(G, eps, 1e-3)
+    ctx.debug_set(nbm.NB_DBG_MATH_VARIANT, variant)
+    a = to_np(ctx.accel(_t(s.x), _t(s.m)))
+    assert rel_l2(a, oracle.accel(s.x, s.m, G, eps)) <= 2e-5
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    ctx.run(x, v, m, 3)
+    xr, _ = oracle.run(s.x, s.v, s.m, G, eps, 1e-3, 3)
+    assert rel_l2(to_np(x), xr) <= 1e-5
+
+
+def test_measured_peaks_are_physical(nbm):
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    p = ctx.measure_peaks()
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    # a plain FMA stream cannot beat the FMA lanes at the maximum clock
+    assert 0.5 * nominal < p["ffma_tflops"] <= 1.02 * nominal
+    assert 0.5 * nominal < p["ffma2_tflops"] <= 1.02 * nominal
+    assert p["mufu_rsqrt_gops"] > 0
