@@ -130,6 +130,19 @@ nb_status fail(nb_ctx *ctx, nb_status s, const char *fmt, ...) {
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Two timing events, destroyed on every exit path.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&e0);
+        return e != cudaSuccess ? e : cudaEventCreate(&e1);
+    }
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 void clear_graphs(nb_ctx *ctx) {
     for (auto &kv : ctx->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -1058,9 +1071,9 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     NB_TRY(ensure(ctx, ctx->tune[2], (size_t)total * 12));
     NB_TRY(ensure(ctx, ctx->tune[3], (size_t)total * 4));
     cudaStream_t st = ctx->side;
-    cudaEvent_t e0, e1;
-    NB_CUDA(cudaEventCreate(&e0));
-    NB_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
+    NB_CUDA(ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     const int probe_steps = 4;
     float best_ms = 1e30f;
     BatchPlan best;
@@ -1092,8 +1105,6 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     NB_TRY(sync_and_check(ctx, st));
     if (best_ms >= 1e30f) return fail(ctx, NB_ERR_CUDA, "no batched shape could be planned");
     ctx->batched_tuned[sizes_signature(off)] = best;
@@ -1147,9 +1158,9 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     NB_TRY(ensure(ctx, ctx->tune[4], (size_t)n * 3 * 8, true));    // abar64
     (void)es;
     cudaStream_t st = ctx->side;
-    cudaEvent_t e0, e1;
-    NB_CUDA(cudaEventCreate(&e0));
-    NB_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
+    NB_CUDA(ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     auto time_shape = [&](const Shape &s, float *ms) -> nb_status {
         Plan p;
         NB_TRY(make_plan(ctx, s, n, &p));
@@ -1202,8 +1213,6 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
             if (ms < best_ms) { best_ms = ms; best = TuneEntry{base.pol, base.nt, base.r, jt, sm}; }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     NB_TRY(sync_and_check(ctx, st));
     ctx->tuned[tune_key(ctx, mode, n)] = best;
     clear_graphs(ctx);
