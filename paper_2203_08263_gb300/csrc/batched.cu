@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
                 }
                 if (!give_up) {
                     const float4 *tile = ring + slot * f4_per_tile;
-#pragma unroll 2
+#pragma unroll(AccelF32x2::UNROLL)
                     for (int jp = 0; jp < (a.jt >> 1); ++jp) {
                         float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
 #pragma unroll

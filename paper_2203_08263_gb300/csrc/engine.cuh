@@ -26,11 +26,14 @@
 
 namespace nb {
 
-#ifndef NB_JP_UNROLL
-#define NB_JP_UNROLL 2  // j-pairs per unrolled step of the tile loop
+// j-pairs per unrolled step of the tile loop, per policy (measured on GB300:
+// 4 for the FP32 forces, 1 for the precision form, 2 elsewhere); a build
+// flag NB_JP_UNROLL overrides all of them.
+#ifdef NB_JP_UNROLL
+#define NB_UNROLL_OR(n) NB_JP_UNROLL
+#else
+#define NB_UNROLL_OR(n) (n)
 #endif
-#define NB_STR(x) #x
-#define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR(unroll n))
 
 #ifndef NB_PRODUCER_WARP
 #define NB_PRODUCER_WARP 0  // 0: consumer thread 0 issues the copies; 1: a dedicated warp does
@@ -143,7 +146,7 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
                                           const typename P::I (&ist)[R], ACC (&acc)[R],
                                           const typename P::C &cst, int64_t jbase, int64_t ibase,
                                           int tid) {
-    NB_PRAGMA_UNROLL(NB_JP_UNROLL)
+#pragma unroll(P::UNROLL)
     for (int jp = 0; jp < jpairs; ++jp) {
         float4 rec[P::REC_F4];
 #pragma unroll
@@ -501,6 +504,7 @@ __device__ __forceinline__ void finish_fp64(const ForceArgs &args, int64_t i, do
 // 1 MUFU rsqrt per interaction: 3 add (d), 3 fma (r^2 + eps^2), 3 mul
 // (m y^3), 3 fma (accumulate).
 struct AccelF32x2 {
+    static constexpr int UNROLL = NB_UNROLL_OR(4);
     static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
@@ -559,6 +563,7 @@ struct AccelF32x2 {
 // Same sum with scalar FP32 instructions (one j-body at a time), kept as the
 // baseline shape the autotuner can compare against.
 struct AccelScalar {
+    static constexpr int UNROLL = NB_UNROLL_OR(2);
     static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
@@ -617,6 +622,7 @@ struct AccelScalar {
 // Scalar FP32; otherwise identical to AccelScalar.
 template <int kMath>
 struct AccelMath {
+    static constexpr int UNROLL = NB_UNROLL_OR(2);
     static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
@@ -664,6 +670,7 @@ struct AccelMath {
 // folded into a (hi, lo) pair with Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
 // update run in FP64.
 struct AccelComp {
+    static constexpr int UNROLL = NB_UNROLL_OR(1);
     static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 2;
@@ -734,6 +741,7 @@ struct AccelComp {
 // epilogue removes the j = i term (m_i / eps, evaluated with the same FP32
 // operations the loop used) and writes m_i * phi_i as a double.
 struct Potential {
+    static constexpr int UNROLL = NB_UNROLL_OR(2);
     static constexpr bool SELF_MASK = false;
     static constexpr int REC_F4 = 2;
     static constexpr int PART_F4 = 1;
@@ -788,6 +796,7 @@ struct Potential {
 // Adjoint records, 4 float4 per pair of bodies:
 //   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,0,0}
 struct VjpF32x2 {
+    static constexpr int UNROLL = NB_UNROLL_OR(2);
     static constexpr bool SELF_MASK = true;
     static constexpr int REC_F4 = 4;
     static constexpr int PART_F4 = 2;
@@ -896,6 +905,7 @@ struct VjpF32x2 {
 // m_k and abar_k. Records, 5 float4 per pair of bodies:
 //   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,xl0,xl1} {yl0,yl1,zl0,zl1}
 struct VjpComp {
+    static constexpr int UNROLL = NB_UNROLL_OR(2);
     static constexpr bool SELF_MASK = true;
     static constexpr int REC_F4 = 5;
     static constexpr int PART_F4 = 4;
