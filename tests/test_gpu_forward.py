@@ -264,3 +264,20 @@ def test_measured_peaks_are_physical(nbm):
     assert 0.5 * nominal < p["ffma_tflops"] <= 1.02 * nominal
     assert 0.5 * nominal < p["ffma2_tflops"] <= 1.02 * nominal
     assert p["mufu_rsqrt_gops"] > 0
+
+
+def test_misaligned_and_foreign_pointers_rejected(nbm):
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    x = torch.zeros(3 * 64 + 1, device=DEV)
+    m = torch.ones(64, device=DEV)
+    lib = nbm.load()
+    a = torch.empty((64, 3), device=DEV)
+    stream = torch.cuda.current_stream().cuda_stream
+    # a float32 array that starts 2 bytes into an allocation
+    st = lib.nb_accel(ctx.h, 64, x.data_ptr() + 2, m.data_ptr(), a.data_ptr(), stream)
+    assert st == nbm.NB_ERR_INVALID
+    assert b"aligned" in lib.nb_last_error(ctx.h)
+    st = lib.nb_accel(ctx.h, 64, None, m.data_ptr(), a.data_ptr(), stream)
+    assert st == nbm.NB_ERR_INVALID
+    assert lib.nb_run(ctx.h, -1, x.data_ptr(), x.data_ptr(), m.data_ptr(), 1, None, 0, stream) == nbm.NB_ERR_INVALID
+    assert lib.nb_run(ctx.h, 64, x.data_ptr(), x.data_ptr(), m.data_ptr(), -3, None, 0, stream) == nbm.NB_ERR_INVALID

@@ -144,3 +144,51 @@ def test_adjoint_midsize_fp32_and_comp(nbm):
         errs = [rel_l2(to_np(g), r) for g, r in zip(got, ref)]
         print(f"adjoint {prec} n={n}: " + " ".join(f"{e:.2e}" for e in errs))
         assert max(errs) <= tol
+
+
+def test_c5_full_size_directional_derivatives(nbm):
+    """Adjoint at the full C5 size (N=16384 cube, seed 4, T=200, k=20): the
+    precision-form gradient's directional derivatives match central
+    differences of the FP64-state forward run, and the plain FP32 gradient
+    agrees with the precision-form one."""
+    n, T, k, G, eps, dt = 16384, 200, 20, 1.0, 0.01, 1e-3
+    s = ics.cube(n, seed=4, masses="equal")
+    xstar = ics.targets(n, seed=4)
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    x0, v0, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    xs = _t(xstar, f)
+
+    def loss(xi, vi, mi):
+        x, v = xi.clone(), vi.clone()
+        ctx.run(x, v, mi, T)
+        return float(((x - xs) ** 2).sum())
+
+    x, v = x0.clone(), v0.clone()
+    ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - xs)
+    gx, gv, gm = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    for g, which, h in ((gx, "x", 1e-4), (gv, "v", 1e-4), (gm, "m", 1e-9)):
+        d = torch.randn(g.shape, generator=gen, dtype=f).to(DEV)
+        args = {"x": x0, "v": v0, "m": m}
+        plus, minus = dict(args), dict(args)
+        plus[which] = args[which] + h * d
+        minus[which] = args[which] - h * d
+        fd = (loss(plus["x"], plus["v"], plus["m"]) - loss(minus["x"], minus["v"], minus["m"])) / (2 * h)
+        ad = float((g * d).sum())
+        print(f"C5 {which}: adjoint {ad:.6e} finite difference {fd:.6e}")
+        assert abs(ad - fd) <= 1e-3 * abs(fd)
+    # the FP32 path's gradient, same problem
+    ctx32 = nbm.Context(G, eps, dt)
+    f32 = torch.float32
+    x, v, m32 = _t(s.x, f32), _t(s.v, f32), _t(s.m, f32)
+    ck32 = torch.empty((T // k + 1, n, 6), dtype=f32, device=DEV)
+    ctx32.run(x, v, m32, T, ckpt=ck32, ckpt_every=k)
+    xb32 = 2 * (x - _t(xstar, f32))
+    g32 = ctx32.adjoint(m32, T, ck32, k, xb32, torch.zeros_like(xb32))
+    for a, b in zip(g32, (gx, gv, gm)):
+        err = rel_l2(to_np(a), to_np(b))
+        print(f"C5 FP32 vs precision-form gradient: {err:.2e}")
+        assert err <= 1e-3
