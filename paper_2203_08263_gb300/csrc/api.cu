@@ -276,7 +276,7 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n) {
         r = 4;
         if (n >= 4096) jt = 128;
     } else if (pol == kPolComp) {
-        r = 2;
+        r = n >= 65536 ? 4 : 2;
         if (n >= 4096) jt = 128;
     } else if (pol == kPolPot) {
         r = 2;
@@ -1198,7 +1198,9 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
             Shape s = finish_shape(ctx, pol, tab[k].nt, tab[k].r, jt, 0, n);
             float ms;
             NB_TRY(time_shape(s, &ms));
-            if (ms < best_ms) { best_ms = ms; best = TuneEntry{pol, tab[k].nt, tab[k].r, jt, 0}; }
+            // a later candidate must win by more than 1 % (keeps the choice
+            // stable against timing noise)
+            if (ms < best_ms * 0.99f) { best_ms = ms; best = TuneEntry{pol, tab[k].nt, tab[k].r, jt, 0}; }
         }
     }
     // refine the tile and split around the winner
@@ -1210,7 +1212,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
             Shape s = finish_shape(ctx, base.pol, base.nt, base.r, jt, sm, n);
             float ms;
             NB_TRY(time_shape(s, &ms));
-            if (ms < best_ms) { best_ms = ms; best = TuneEntry{base.pol, base.nt, base.r, jt, sm}; }
+            if (ms < best_ms * 0.99f) { best_ms = ms; best = TuneEntry{base.pol, base.nt, base.r, jt, sm}; }
         }
     }
     NB_TRY(sync_and_check(ctx, st));
