@@ -191,6 +191,27 @@ def fp32_peak_tflops(props, sm_max_mhz):
     return props.multi_processor_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
+def use_shipped_tuning_table(torch, device: int) -> str:
+    """Point the library at the tuner's table for this GPU type, when the
+    package ships one (written by paper_2203_08263_gb300.tune_table on this
+    GPU type): launch shapes then come from the tuner and are reproducible.
+    A private copy is used so that no run rewrites the shipped file."""
+    import shutil
+
+    from paper_2203_08263_gb300.tune_table import table_path
+
+    if os.environ.get("NB_AUTOTUNE_CACHE"):
+        return "NB_AUTOTUNE_CACHE"
+    src = table_path(torch.cuda.get_device_name(device))
+    if not os.path.exists(src):
+        return "none"
+    fd, tmp = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    shutil.copyfile(src, tmp)
+    os.environ["NB_AUTOTUNE_CACHE"] = tmp
+    return "tuner table shipped for this GPU type"
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -206,10 +227,13 @@ def run_ours(args):
     from paper_2203_08263_gb300.nbody import Context
 
     nbuild.build()
+    shape_source = use_shipped_tuning_table(torch, local)
     n, G, eps, dt = args.n, 1.0, 0.05, 1e-3
     s = ics.plummer(n, seed=1)
     ctx = Context(G, eps, dt, device=local)
-    ctx.autotune(n)
+    if not ctx.get_config(n)["tuned"]:
+        ctx.autotune(n)
+        shape_source = "tuned in this run"
     cfg = ctx.get_config(n)
     x = torch.tensor(s.x, dtype=torch.float32, device=dev)
     v = torch.tensor(s.v, dtype=torch.float32, device=dev)
@@ -285,7 +309,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload(n), "n": n, "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "shape": cfg},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "shape": cfg,
+                   "shape_source": shape_source},
         "roofline": roofline,
         "interactions_per_s_per_gpu": inter * args.steps / (tot_ms / 1e3),
         "gflops_20": FLOPS_PER_INTERACTION * value / 1e9,
@@ -372,6 +397,9 @@ def extras(ctx0, torch, dev, np):
     s = ics.cube(n, seed=4, masses="equal")
     xs = ics.targets(n, seed=4)
     c = Context(1.0, 0.01, 1e-3, device=dev.index)
+    for mode in (0, 1):  # forward and VJP shapes from the tuner
+        if not c.get_config(n, mode)["tuned"]:
+            c.autotune(n, mode)
     x0, v0, m = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (s.x, s.v, s.m))
     ck = torch.empty((T // k + 1, n, 6), dtype=torch.float32, device=dev)
     x, v = x0.clone(), v0.clone()
@@ -388,7 +416,8 @@ def extras(ctx0, torch, dev, np):
     tf = _timed(torch, dev, fwd)
     tb = _timed(torch, dev, lambda: c.adjoint(m, T, ck, k, xbT, vbT))
     out["c5_adjoint"] = {"n": n, "T": T, "k": k, "forward_s": tf, "backward_s": tb, "ratio": tb / tf,
-                         "forward_interactions_per_s": float(n) * n * T / tf}
+                         "forward_interactions_per_s": float(n) * n * T / tf,
+                         "forward_shape": c.get_config(n, 0), "vjp_shape": c.get_config(n, 1)}
     c.close()
     out["cpu_oracle_rows"] = oracle_rows()
     out["fp32_peak_fraction"] = {

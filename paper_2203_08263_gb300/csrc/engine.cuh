@@ -165,12 +165,12 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
     }
 }
 
-// Register caps: 512 resident threads per SM at R <= 4 (<= 128 registers),
-// and three 128-thread CTAs per SM at R = 8 (<= 170 registers; 166 needed,
-// no spills), i.e. 12 warps per SM instead of 8 for the largest tiles.
+// Register caps: 512 resident threads per SM at R <= 4 (<= 128 registers).
+// R = 8 stays uncapped: capping 128 x 8 tiles to 3 CTAs per SM (166
+// registers) measured 5 % slower than 2 CTAs at 210 registers.
 template <int NT, int R>
 constexpr int min_blocks() {
-    return NB_PRODUCER_WARP ? 1 : (R <= 4 ? 512 / NT : (NT == 128 ? 3 : 1));
+    return (NB_PRODUCER_WARP || R > 4) ? 1 : 512 / NT;
 }
 
 template <int NT, int R, class P>
