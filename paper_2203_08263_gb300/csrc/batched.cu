@@ -64,11 +64,17 @@ __device__ bool wait_at_least(const unsigned *p, unsigned target, uint64_t timeo
     return true;
 }
 
+// Ring of the batched kernel: deeper than the single-system kernel's, and
+// refilled with a lag of two tiles, so that thread 0 rarely waits for the
+// slowest warp on the short tiles of small systems.
+constexpr int kBS = 8;           // slots
+constexpr int kLead = kBS - 2;   // tiles issued ahead of the one being consumed
+
 template <int NT, int R>
 __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
-    uint64_t *empty = full + kStages;
+    uint64_t *empty = full + kBS;
     float4 *ring = reinterpret_cast<float4 *>(smem_raw + 128);
     __shared__ unsigned s_item;
     __shared__ int s_abort;
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     const unsigned total = (unsigned)a.items_per_step * (unsigned)a.steps;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kBS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NT / 32);
         }
@@ -89,16 +95,16 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     __syncthreads();
 
     // Ring position q (tiles streamed so far by this CTA) runs on across
-    // items; slot q % kStages, phase q / kStages. Thread 0 issues position q
-    // once position q - kStages has been released by every warp.
+    // items; slot q % kBS, phase q / kBS. Thread 0 issues position q
+    // once position q - kBS has been released by every warp.
     uint32_t kk = 0;       // position of the current item's first tile
     uint32_t issued = 0;   // positions issued so far (thread 0)
     bool give_up = false;  // a ring wait failed: stop streaming
 
     auto issue = [&](uint32_t q, const float4 *src_tile) {
-        const int slot = q % kStages;
-        if (q >= (uint32_t)kStages &&
-            !mbar_wait(&empty[slot], ((q / kStages) - 1) & 1, a.timeout_ns)) {
+        const int slot = q % kBS;
+        if (q >= (uint32_t)kBS &&
+            !mbar_wait(&empty[slot], ((q / kBS) - 1) & 1, a.timeout_ns)) {
             atomicOr(a.err, kErrEmptyWait);
             give_up = true;
             return;
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
         __syncthreads();
         const bool run = !s_abort && !give_up;
         if (tid == 0 && run)
-            for (int q = 0; q < ntl && q < kStages - 1 && !give_up; ++q)
+            for (int q = 0; q < ntl && q < kLead && !give_up; ++q)
                 issue(kk + q, src + (int64_t)q * f4_per_tile);
         AccelF32x2::I ist[R];
         AccelF32x2::T tot[R];
@@ -163,8 +169,8 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
         if (run) {
             for (int q = 0; q < ntl; ++q) {
                 const uint32_t pos = kk + q;
-                const int slot = pos % kStages;
-                if (!give_up && !mbar_wait(&full[slot], (pos / kStages) & 1, a.timeout_ns)) {
+                const int slot = pos % kBS;
+                if (!give_up && !mbar_wait(&full[slot], (pos / kBS) & 1, a.timeout_ns)) {
                     atomicOr(a.err, kErrFullWait);
                     give_up = true;
                 }
@@ -179,9 +185,9 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&empty[slot]);
                 }
-                // refill: position pos + kStages - 1 goes into the slot of pos - 1
-                if (tid == 0 && !give_up && q + kStages - 1 < ntl)
-                    issue(pos + kStages - 1, src + (int64_t)(q + kStages - 1) * f4_per_tile);
+                // refill: position pos + kLead goes into the slot of pos - 2
+                if (tid == 0 && !give_up && q + kLead < ntl)
+                    issue(pos + kLead, src + (int64_t)(q + kLead) * f4_per_tile);
             }
             kk += ntl;
 #pragma unroll
@@ -214,8 +220,8 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     }
     // never leave while our own copies may still be landing
     if (tid == 0) {
-        for (uint32_t q = issued > (uint32_t)kStages ? issued - kStages : 0; q < issued; ++q) {
-            if (!mbar_wait(&full[q % kStages], (q / kStages) & 1, kDrainTimeoutNs))
+        for (uint32_t q = issued > (uint32_t)kBS ? issued - kBS : 0; q < issued; ++q) {
+            if (!mbar_wait(&full[q % kBS], (q / kBS) & 1, kDrainTimeoutNs))
                 atomicOr(a.err, kErrDrain);
         }
     }
@@ -255,7 +261,7 @@ __global__ void batched_fill_kernel(const int64_t *off, float *x, float *v, floa
 
 template <int NT, int R>
 size_t batched_smem(int jt) {
-    return 128 + (size_t)kStages * jt * 16;
+    return 128 + (size_t)kBS * jt * 16;
 }
 
 // Device copy of the plan inside the scratch block.
