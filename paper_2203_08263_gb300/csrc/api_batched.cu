@@ -1,0 +1,158 @@
+// libnbody C-ABI: ensembles of independent systems in one persistent launch,
+// and their tuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace nb;
+using namespace nb::detail;
+
+extern "C" {
+
+int64_t nb_batched_max_n(void) { return batched_max_n(); }
+
+nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
+                         const void *m, int steps, void *stream) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (nsys < 0 || steps < 0) return fail(ctx, NB_ERR_INVALID, "nsys < 0 or steps < 0");
+    if (nsys == 0 || steps == 0) return NB_OK;
+    if (f64_state(ctx)) return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs are FP32 only");
+    if (ctx->p.scheme != NB_SCHEME_PAPER)
+        return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs use the paper scheme");
+    if (!offsets) return fail(ctx, NB_ERR_INVALID, "offsets is NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, as_stream(stream), off));
+    const int64_t total = off[nsys];
+    if (total == 0) return NB_OK;
+    if (steps > (1 << 20)) return fail(ctx, NB_ERR_INVALID, "at most 2^20 steps per batched call");
+    NB_TRY(check_ptr(ctx, x, 4, "x", nullptr));
+    NB_TRY(check_ptr(ctx, v, 4, "v", nullptr));
+    NB_TRY(check_ptr(ctx, m, 4, "m", nullptr));
+    cudaStream_t st = as_stream(stream);
+    BatchPlan plan;
+    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
+    if (tuned != ctx->batched_tuned.end()) {
+        plan.nt = tuned->second.nt;
+        plan.r = tuned->second.r;
+        plan.jt = tuned->second.jt;
+    }
+    std::string why;
+    if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
+        return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
+    NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
+    NB_CUDA(batched_upload(plan, ctx->bat.p, st));
+    char key[512];
+    snprintf(key, sizeof key, "bat|%d|%p|%p|%p|%d|%lld|%llx|%llu|%a|%a|%a", nsys, x, v, m, steps,
+             (long long)total, (unsigned long long)plan.signature,
+             (unsigned long long)ctx->timeout_ns, ctx->p.G, ctx->p.eps, ctx->p.dt);
+    GraphEntry *g = graph_lookup(ctx, key);
+    if (!g) {
+        NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = batched_enqueue(plan, ctx->bat.p, (float *)x, (float *)v, (const float *)m,
+                                         steps, (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
+                                         (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, ctx->side);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce2 = cudaStreamEndCapture(ctx->side, &graph);
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(ctx, NB_ERR_CUDA, "batched capture: %s",
+                        cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        }
+        cudaGraphExec_t ex = nullptr;
+        ce = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(ctx, NB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        graph_insert(ctx, key, ex, plan.launches);
+        g = graph_lookup(ctx, key);
+    }
+    NB_CUDA(cudaGraphLaunch(g->exec, st));
+    ctx->launches += g->nodes;
+    return NB_OK;
+}
+
+nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    const int64_t total = off[nsys];
+    if (total == 0) return NB_OK;
+    NB_TRY(ensure(ctx, ctx->tune[1], (size_t)total * 12));
+    NB_TRY(ensure(ctx, ctx->tune[2], (size_t)total * 12));
+    NB_TRY(ensure(ctx, ctx->tune[3], (size_t)total * 4));
+    cudaStream_t st = ctx->side;
+    EventPair ev;
+    NB_CUDA(ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
+    const int probe_steps = 4;
+    float best_ms = 1e30f;
+    BatchPlan best;
+    for (int r : {1, 2, 4}) {
+        for (int jt : {64, 128}) {
+            BatchPlan plan;
+            plan.r = r;
+            plan.jt = jt;
+            std::string why;
+            if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
+            NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
+            NB_CUDA(batched_upload(plan, ctx->bat.p, st));
+            float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
+            NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
+            const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, eps2, (float)ctx->p.G,
+                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(cudaEventRecord(e0, st));
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, eps2, (float)ctx->p.G,
+                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(cudaEventRecord(e1, st));
+            NB_CUDA(cudaEventSynchronize(e1));
+            ctx->launches += 6;
+            float ms = 0.f;
+            NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = plan;
+            }
+        }
+    }
+    NB_TRY(sync_and_check(ctx, st));
+    if (best_ms >= 1e30f) return fail(ctx, NB_ERR_CUDA, "no batched shape could be planned");
+    ctx->batched_tuned[sizes_signature(off)] = best;
+    clear_graphs(ctx);
+    return NB_OK;
+}
+
+nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6) {
+    if (!ctx || !out6) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    BatchPlan plan;
+    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
+    const bool from_tune = tuned != ctx->batched_tuned.end();
+    if (from_tune) {
+        plan.r = tuned->second.r;
+        plan.jt = tuned->second.jt;
+    }
+    std::string why;
+    if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
+        return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
+    out6[0] = plan.nt;
+    out6[1] = plan.r;
+    out6[2] = plan.jt;
+    out6[3] = plan.items_per_step;
+    out6[4] = plan.ncta;
+    out6[5] = from_tune ? 1 : 0;
+    return NB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// libnbody C-ABI: the launch-shape tuner and shape queries.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace nb;
+using namespace nb::detail;
+
+extern "C" {
+
+nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (n <= 0) return fail(ctx, NB_ERR_INVALID, "n must be > 0");
+    if (mode != 0 && mode != 1) return fail(ctx, NB_ERR_INVALID, "mode must be 0 or 1");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int> pols;
+    if (mode == 0) {
+        if (f64_state(ctx)) pols = {kPolComp};
+        else pols = {kPolF32x2, kPolScalar};
+    } else {
+        pols = {f64_state(ctx) ? kPolVjpComp : kPolVjp};
+    }
+    const int64_t npad = round_up(n, kPadBodies);
+    const size_t es = esize(ctx);
+    NB_TRY(ensure(ctx, ctx->tune[0], (size_t)npad * 40));          // records
+    NB_TRY(ensure(ctx, ctx->tune[1], (size_t)n * 3 * 8, true));    // out / xbar
+    NB_TRY(ensure(ctx, ctx->tune[2], (size_t)n * 8, true));        // mbar
+    NB_TRY(ensure(ctx, ctx->tune[3], (size_t)n * 8, true));        // mass
+    NB_TRY(ensure(ctx, ctx->tune[4], (size_t)n * 3 * 8, true));    // abar64
+    (void)es;
+    cudaStream_t st = ctx->side;
+    EventPair ev;
+    NB_CUDA(ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
+    auto time_shape = [&](const Shape &s, float *ms) -> nb_status {
+        Plan p;
+        NB_TRY(make_plan(ctx, s, n, &p));
+        if (p.part_bytes > ((size_t)1 << 31)) { *ms = 1e30f; return NB_OK; }
+        NB_TRY(plan_scratch(ctx, p));
+        NB_CUDA(launch_fill_synthetic(n, npad, (float4 *)ctx->tune[0].p, pol_rec_f4(s.pol), st));
+        ForceArgs a = base_args(ctx, p, n, (const float4 *)ctx->tune[0].p);
+        a.op = mode == 0 ? kEpiAccel : kEpiVjp;
+        a.out = ctx->tune[1].p;
+        a.xbar = ctx->tune[1].p;
+        a.mbar = ctx->tune[2].p;
+        a.mass = ctx->tune[3].p;
+        a.abar64 = ctx->tune[4].p;
+        NB_CUDA(p.e->launch(s.jt, a, st));  // warm-up
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            NB_CUDA(cudaEventRecord(e0, st));
+            NB_CUDA(p.e->launch(s.jt, a, st));
+            NB_CUDA(cudaEventRecord(e1, st));
+            NB_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            NB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return NB_OK;
+    };
+    TuneEntry best{};
+    float best_ms = 1e30f;
+    for (int pol : pols) {
+        int cnt = 0;
+        const ForceEntry *tab = force_table(pol, &cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int jt = npad >= 4096 ? 128 : 64;
+            Shape s = finish_shape(ctx, pol, tab[k].nt, tab[k].r, jt, 0, n);
+            float ms;
+            NB_TRY(time_shape(s, &ms));
+            // a later candidate must win by more than 1 % (keeps the choice
+            // stable against timing noise)
+            if (ms < best_ms * 0.99f) { best_ms = ms; best = TuneEntry{pol, tab[k].nt, tab[k].r, jt, 0}; }
+        }
+    }
+    // refine the tile and split around the winner
+    const TuneEntry base = best;
+    for (int jt : {64, 128, 256}) {
+        for (int sm : {-1, 0, 1}) {
+            if (jt == base.jt && sm == 0) continue;
+            if (npad % jt) continue;
+            Shape s = finish_shape(ctx, base.pol, base.nt, base.r, jt, sm, n);
+            float ms;
+            NB_TRY(time_shape(s, &ms));
+            if (ms < best_ms * 0.99f) { best_ms = ms; best = TuneEntry{base.pol, base.nt, base.r, jt, sm}; }
+        }
+    }
+    NB_TRY(sync_and_check(ctx, st));
+    ctx->tuned[tune_key(ctx, mode, n)] = best;
+    clear_graphs(ctx);
+    save_tune_file(ctx);
+    return NB_OK;
+}
+
+nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5) {
+    if (!ctx || !out5) return NB_ERR_INVALID;
+    if (mode < 0 || mode > 2) return fail(ctx, NB_ERR_INVALID, "mode must be 0, 1 or 2");
+    Shape s;
+    bool tuned = false;
+    NB_TRY(choose_shape(ctx, mode, std::max<int64_t>(n, 1), &s, &tuned));
+    out5[0] = s.nt;
+    out5[1] = s.r;
+    out5[2] = s.split;
+    out5[3] = s.jt;
+    out5[4] = tuned ? 1 : 0;
+    return NB_OK;
+}
+
+}  // extern "C"
