@@ -134,8 +134,10 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * nsys+1 entries, offsets[0] = 0, non-decreasing) may be a host or a device
  * pointer. Systems do not interact. Each system's size must be at most
  * nb_batched_max_n(); steps at most 2^20 per call. FP32 precision only.
- * Inside the launch, work items (system, step, chunk of i-bodies) are taken
- * from one queue; a step of a system starts when its previous step is done.
+ * Inside the launch, work items (system, step, chunk of T x R i-bodies for
+ * T threads per CTA; R = 8, 4, 2 or 1 per item: full chunks at the shape's
+ * largest R, a system's ragged rest in smaller ones) are taken from one
+ * queue; a step of a system starts when its previous step is done.
  */
 nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
                          const void *m, int steps, void *stream);
@@ -152,10 +154,22 @@ int64_t nb_batched_max_n(void);
 nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets);
 
 /* The batched launch the context would use for these sizes: out[0..5] =
- * {threads per CTA, bodies per thread, j-tile bodies, work items per step,
- * CTAs in the persistent grid, 1 if the shape came from
- * nb_autotune_batched}. */
+ * {threads per CTA, largest bodies per thread of an item, j-tile bodies, work
+ * items per step, CTAs in the persistent grid, origin of the shape: 0 the
+ * default, 1 nb_autotune_batched, 2 nb_set_batched_config}. */
 nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6);
+
+/*
+ * Pin the batched launch shape for this size profile (offsets as for
+ * nb_run_batched): threads per CTA and the largest R of an item, one of
+ * 128 or 256 x {1, 2, 4, 8} or 512 x {1, 2}, and jtile, the j-bodies per
+ * streamed tile (32, 64, 128 or 256). All three 0 removes a pinned or tuned
+ * shape (back to the default). NB_ERR_INVALID for other values. Replaces
+ * what nb_autotune_batched chose for these sizes. A tuning interface of this
+ * library; the paper has no counterpart.
+ */
+nb_status nb_set_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int threads,
+                                int bodies_per_thread, int jtile);
 
 /*
  * Reverse mode of nb_run with the paper scheme. Given the checkpoints written

@@ -95,10 +95,13 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     const int probe_steps = 4;
     float best_ms = 1e30f;
     BatchPlan best;
-    for (int r : {1, 2, 4}) {
+    static const int kShapes[][2] = {{128, 1}, {128, 2}, {128, 4}, {128, 8}, {256, 1},
+                                     {256, 2}, {256, 4}, {256, 8}, {512, 1}, {512, 2}};
+    for (const auto &shape : kShapes) {
         for (int jt : {64, 128}) {
             BatchPlan plan;
-            plan.r = r;
+            plan.nt = shape[0];
+            plan.r = shape[1];
             plan.jt = jt;
             std::string why;
             if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
@@ -125,6 +128,7 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     }
     NB_TRY(sync_and_check(ctx, st));
     if (best_ms >= 1e30f) return fail(ctx, NB_ERR_CUDA, "no batched shape could be planned");
+    best.origin = 1;
     ctx->batched_tuned[sizes_signature(off)] = best;
     clear_graphs(ctx);
     return NB_OK;
@@ -138,10 +142,11 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
     BatchPlan plan;
     auto tuned = ctx->batched_tuned.find(sizes_signature(off));
-    const bool from_tune = tuned != ctx->batched_tuned.end();
-    if (from_tune) {
+    if (tuned != ctx->batched_tuned.end()) {
+        plan.nt = tuned->second.nt;
         plan.r = tuned->second.r;
         plan.jt = tuned->second.jt;
+        plan.origin = tuned->second.origin;
     }
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
@@ -151,7 +156,42 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     out6[2] = plan.jt;
     out6[3] = plan.items_per_step;
     out6[4] = plan.ncta;
-    out6[5] = from_tune ? 1 : 0;
+    out6[5] = plan.origin;
+    return NB_OK;
+}
+
+nb_status nb_set_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int threads,
+                                int bodies_per_thread, int jtile) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    const uint64_t sig = sizes_signature(off);
+    if (threads == 0 && bodies_per_thread == 0 && jtile == 0) {
+        ctx->batched_tuned.erase(sig);
+        clear_graphs(ctx);
+        return NB_OK;
+    }
+    const bool r_any = bodies_per_thread == 1 || bodies_per_thread == 2 || bodies_per_thread == 4 ||
+                       bodies_per_thread == 8;
+    const bool shape_ok = ((threads == 128 || threads == 256) && r_any) ||
+                          (threads == 512 && (bodies_per_thread == 1 || bodies_per_thread == 2));
+    if (!shape_ok)
+        return fail(ctx, NB_ERR_INVALID,
+                    "threads x bodies_per_thread must be 128 or 256 x {1,2,4,8}, or 512 x {1,2}");
+    if (jtile != 32 && jtile != 64 && jtile != 128 && jtile != 256)
+        return fail(ctx, NB_ERR_INVALID, "jtile must be 32, 64, 128 or 256");
+    BatchPlan plan;
+    plan.nt = threads;
+    plan.r = bodies_per_thread;
+    plan.jt = jtile;
+    std::string why;
+    if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
+        return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
+    plan.origin = 2;
+    ctx->batched_tuned[sig] = plan;
+    clear_graphs(ctx);
     return NB_OK;
 }
 

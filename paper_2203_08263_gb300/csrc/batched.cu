@@ -1,20 +1,21 @@
 // Persistent ensemble kernel: every system of the batch advances `steps`
 // paper steps inside one cooperative launch, as a dataflow over work items
-// (system, step, i-chunk). Persistent CTAs pop items from one atomic queue in
-// step-major order (largest systems first within a step); an item waits,
-// bounded, until every item of the previous step of its own system is done,
-// then computes the forces on its i-chunk from all j-bodies of the system
-// (j-tiles streamed by 1-D bulk copies, issued by thread 0, through a
-// shared-memory ring as in the single-system kernel), applies the half kick
-// and the drift, writes the repacked positions to the other buffer and
-// releases itself. The oldest unfinished item never waits, so the queue
-// always makes progress, and load balance is within one item.
+// (system, step, i-chunk of NT x R bodies, R per item). Persistent CTAs take
+// items from one atomic queue in step-major order (most work first within a
+// step) and hold a few; an item is ready once every item of the previous
+// step of its own system is done. A CTA runs its lowest-numbered ready item:
+// the forces on its i-chunk from all j-bodies of the system (j-tiles streamed
+// by 1-D bulk copies through a shared-memory ring), the half kick and the
+// drift, the repacked positions written to the other buffer; then it
+// releases the item. The lowest unfinished item is always ready, so the
+// queue always makes progress, and load balance is within one item.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <functional>
 #include <map>
 #include <numeric>
+#include <type_traits>
 
 #include "batched.h"
 #include "engine.cuh"
@@ -25,7 +26,8 @@ namespace {
 
 struct BatchArgs {
     const int64_t *off, *poff;
-    const int *item_sys, *item_chunk, *nchunks;
+    const int *item_sys, *item_lo, *item_r;  // per item of one step
+    const int *nitems;                        // [nsys] items per step
     unsigned *next;  // queue head
     unsigned *done;  // [nsys] items completed, cumulative over steps
     float4 *xm0, *xm1;
@@ -36,14 +38,14 @@ struct BatchArgs {
     uint64_t timeout_ns;
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Order this thread's earlier shared-memory accesses (and those it has
+// acquired from other threads) before later bulk copies into shared memory.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Pair-layout scalar read through L2 only: another CTA may have written it
@@ -53,31 +55,49 @@ __device__ __forceinline__ float pair_get_cg(const float4 *base, int64_t i, int 
     return __ldcg(p + 2 * c + (int)(i & 1));
 }
 
-// Bounded wait until *p >= target; false on timeout.
-__device__ bool wait_at_least(const unsigned *p, unsigned target, uint64_t timeout_ns) {
-    if (ld_acquire(p) >= target) return true;
-    const uint64_t t0 = global_ns();
-    while (ld_acquire(p) < target) {
-        __nanosleep(64);
-        if (global_ns() - t0 > timeout_ns) return false;
-    }
-    return true;
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Ring of the batched kernel: deeper than the single-system kernel's, and
-// refilled with a lag of two tiles, so that thread 0 rarely waits for the
-// slowest warp on the short tiles of small systems.
-constexpr int kBS = 8;           // slots
-constexpr int kLead = kBS - 2;   // tiles issued ahead of the one being consumed
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 
-template <int NT, int R>
-__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const BatchArgs a) {
+
+// Ring of the batched kernel: kBS slots. A slot is refilled by the lane 0 of
+// the last warp to finish with it (a shared counter per slot), the moment it
+// is free, with the tile kBS positions ahead; nobody waits for a free slot,
+// and no warp's own progress decides when the others' tiles arrive.
+constexpr int kBS = 8;
+constexpr int kHold = 4;                  // items a CTA may hold unstarted
+constexpr unsigned kNoItem = 0xFFFFFFFFu;
+
+// Registers are allocated for the largest R the kernel holds. The occupancy
+// hint asks for 512 resident threads per SM up to R = 2 (at most 128
+// registers), 256 at R = 4 and 128 at R = 8 (as the single-system kernel of
+// those shapes); a 512-thread CTA is then alone on its SM.
+template <int NT, int RMAX>
+constexpr int batched_min_blocks() {
+    constexpr int per_sm = RMAX <= 2 ? 512 : (RMAX == 4 ? 256 : 128);
+    return per_sm / NT > 1 ? per_sm / NT : 1;
+}
+
+template <int NT, int RMAX>
+__global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_kernel(const BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
-    uint64_t *empty = full + kBS;
     float4 *ring = reinterpret_cast<float4 *>(smem_raw + 128);
     __shared__ unsigned s_item;
     __shared__ int s_abort;
+    __shared__ unsigned s_rel[kBS];  // warps done with the slot's current tile
+    __shared__ unsigned s_issued;    // ring positions issued so far
+    // Items this CTA has taken from the queue but not started (thread 0
+    // only): number, system, and the completion count of the system that
+    // makes it ready (0: ready at once).
+    __shared__ unsigned h_id[kHold], h_need[kHold];
+    __shared__ int h_sys[kHold];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int f4_per_tile = a.jt;  // (jt / 2) records x 2 float4
@@ -88,71 +108,107 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
     if (tid == 0) {
         for (int s = 0; s < kBS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NT / 32);
+            s_rel[s] = 0;
         }
+        for (int h = 0; h < kHold; ++h) h_id[h] = kNoItem;
+        s_issued = 0;
         mbar_init_fence();
     }
     __syncthreads();
 
     // Ring position q (tiles streamed so far by this CTA) runs on across
-    // items; slot q % kBS, phase q / kBS. Thread 0 issues position q
-    // once position q - kBS has been released by every warp.
-    uint32_t kk = 0;       // position of the current item's first tile
-    uint32_t issued = 0;   // positions issued so far (thread 0)
+    // items; slot q % kBS, phase q / kBS. Position q is issued only once
+    // position q - kBS has been released by every warp: at the start of an
+    // item (every earlier position is released then) or by the last warp to
+    // release q - kBS.
+    int nheld = 0;           // thread 0: items held
+    bool exhausted = false;  // thread 0: the queue is empty
+    uint32_t kk = 0;         // position of the current item's first tile
     bool give_up = false;  // a ring wait failed: stop streaming
 
     auto issue = [&](uint32_t q, const float4 *src_tile) {
         const int slot = q % kBS;
-        if (q >= (uint32_t)kBS &&
-            !mbar_wait(&empty[slot], ((q / kBS) - 1) & 1, a.timeout_ns)) {
-            atomicOr(a.err, kErrEmptyWait);
-            give_up = true;
-            return;
-        }
         mbar_arrive_expect_tx(&full[slot], tile_bytes);
         bulk_g2s(ring + slot * f4_per_tile, src_tile, tile_bytes, &full[slot]);
-        issued = q + 1;
+        atomicMax(&s_issued, q + 1);
     };
 
-    // Thread 0 takes the next item number one item ahead, so the queue's
-    // atomic latency overlaps the current item. Holding one unstarted item
-    // cannot stall the queue: the lowest unfinished item is always one that
-    // some CTA is running, and its dependencies are all finished.
-    unsigned next_id = tid == 0 ? atomicAdd(a.next, 1u) : 0u;
-    for (;;) {
-        if (tid == 0) {
-            s_item = next_id;
-            s_abort = 0;
+    // Thread 0: take one more item from the queue into a free hold slot.
+    auto claim = [&]() {
+        if (exhausted || nheld >= kHold) return;
+        const unsigned id = atomicAdd(a.next, 1u);
+        if (id >= total) {
+            exhausted = true;
+            return;
         }
-        __syncthreads();
-        const unsigned id = s_item;
-        if (id >= total) break;
-        const int t = (int)(id / (unsigned)a.items_per_step);
-        const int k = (int)(id % (unsigned)a.items_per_step);
-        const int s = a.item_sys[k];
-        const int c = a.item_chunk[k];
-        const int64_t b0 = a.off[s];
-        const int64_t n = a.off[s + 1] - b0;
-        const int64_t p0 = a.poff[s];
-        const int ntl = (int)((n + a.jt - 1) / a.jt);
-        const int64_t lo = (int64_t)c * NT * R;
-        const int64_t hi = lo + (int64_t)NT * R < n ? lo + (int64_t)NT * R : n;
-        const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
-        float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
-        if (tid == 0) {
-            // step t of system s needs every item of its step t-1
-            if (t > 0 && !wait_at_least(a.done + s, (unsigned)t * (unsigned)a.nchunks[s], a.timeout_ns)) {
-                atomicOr(a.err, kErrGang);
-                s_abort = 1;
+        const unsigned t = id / (unsigned)a.items_per_step;
+        const int sys = a.item_sys[id % (unsigned)a.items_per_step];
+        for (int h = 0; h < kHold; ++h)
+            if (h_id[h] == kNoItem) {
+                h_id[h] = id;
+                h_sys[h] = sys;
+                h_need[h] = t * (unsigned)a.nitems[sys];  // step t needs all of step t-1
+                ++nheld;
+                return;
             }
-            fence_proxy_async_global();
-            next_id = atomicAdd(a.next, 1u);
+    };
+
+    // Thread 0: the next item to run. Runs the lowest-numbered held item
+    // whose system has finished the previous step; while none is ready and a
+    // hold slot is free, takes more items from the queue; otherwise polls,
+    // bounded. Returns total when the queue is empty and nothing is held.
+    // The lowest unfinished item of the whole launch is always ready (its
+    // predecessors have lower numbers), and whoever holds it runs it at its
+    // next pick, so the queue cannot stall; a CTA never idles on a system that
+    // fell behind while later items of other systems are ready.
+    auto pick = [&](bool &abort) -> unsigned {
+        abort = false;
+        uint64_t t0 = 0;
+        for (;;) {
+            int best = -1;
+            for (int h = 0; h < kHold; ++h) {
+                const unsigned id = h_id[h];
+                if (id == kNoItem || (best >= 0 && id > h_id[best])) continue;
+                if (h_need[h] == 0 || ld_relaxed(a.done + h_sys[h]) >= h_need[h]) best = h;
+            }
+            if (best >= 0) {
+                const unsigned id = h_id[best];
+                h_id[best] = kNoItem;
+                --nheld;
+                fence_acq_rel_gpu();  // the predecessors' writes happen before this item's reads
+                return id;
+            }
+            if (!exhausted && nheld < kHold) {
+                claim();
+                continue;
+            }
+            if (nheld == 0) return total;
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > a.timeout_ns) {
+                // give up on the lowest held item: skipped, but released
+                int low = -1;
+                for (int h = 0; h < kHold; ++h)
+                    if (h_id[h] != kNoItem && (low < 0 || h_id[h] < h_id[low])) low = h;
+                const unsigned id = h_id[low];
+                h_id[low] = kNoItem;
+                --nheld;
+                atomicOr(a.err, kErrGang);
+                abort = true;
+                return id;
+            }
+            __nanosleep(64);
         }
-        __syncthreads();
-        const bool run = !s_abort && !give_up;
-        if (tid == 0 && run)
-            for (int q = 0; q < ntl && q < kLead && !give_up; ++q)
-                issue(kk + q, src + (int64_t)q * f4_per_tile);
+    };
+
+    // One work item with R i-bodies per thread: forces on bodies [lo, hi)
+    // of one system from its ntl j-tiles (Eq. 1 with softening), then the
+    // printed update (half kick v += a dt/2, drift x += v dt with the new
+    // v), and the repacked position written to the other buffer. A generic
+    // lambda, instantiated for each R the kernel holds.
+    auto run_item = [&](auto r_const, const float4 *src, float4 *dst, int64_t b0, int64_t lo,
+                        int64_t hi, int ntl) {
+        constexpr int R = decltype(r_const)::value;
         AccelF32x2::I ist[R];
         AccelF32x2::T tot[R];
         AccelF32x2::C cst;
@@ -166,50 +222,101 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
             ist[r].nz = dup(-pair_get_cg(src, i, 2));
             AccelF32x2::zero_total(tot[r]);
         }
-        if (run) {
-            for (int q = 0; q < ntl; ++q) {
-                const uint32_t pos = kk + q;
-                const int slot = pos % kBS;
-                if (!give_up && !mbar_wait(&full[slot], (pos / kBS) & 1, a.timeout_ns)) {
-                    atomicOr(a.err, kErrFullWait);
-                    give_up = true;
-                }
-                if (!give_up) {
-                    const float4 *tile = ring + slot * f4_per_tile;
+        for (int q = 0; q < ntl; ++q) {
+            const uint32_t pos = kk + q;
+            const int slot = pos % kBS;
+            if (tid == 0 && q == ntl - 1) claim();  // queue latency hidden behind the last tile
+            if (!give_up && !mbar_wait(&full[slot], (pos / kBS) & 1, a.timeout_ns)) {
+                atomicOr(a.err, kErrFullWait);
+                give_up = true;
+            }
+            if (!give_up) {
+                const float4 *tile = ring + slot * f4_per_tile;
 #pragma unroll(AccelF32x2::UNROLL)
-                    for (int jp = 0; jp < (a.jt >> 1); ++jp) {
-                        float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
+                for (int jp = 0; jp < (a.jt >> 1); ++jp) {
+                    float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
 #pragma unroll
-                        for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty[slot]);
+                    for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
                 }
-                // refill: position pos + kLead goes into the slot of pos - 2
-                if (tid == 0 && !give_up && q + kLead < ntl)
-                    issue(pos + kLead, src + (int64_t)(q + kLead) * f4_per_tile);
-            }
-            kk += ntl;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int64_t i = lo + r * NT + tid;
-                if (i < hi) {
-                    const float acc[3] = {a.G * (tot[r].x.x + tot[r].x.y), a.G * (tot[r].y.x + tot[r].y.y),
-                                          a.G * (tot[r].z.x + tot[r].z.y)};
-                    float *xp = a.x + 3 * (b0 + i);
-                    float *vp = a.v + 3 * (b0 + i);
-                    float xs[3];
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        // v += a dt/2 (the printed half kick); x += v dt
-                        const float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
-                        vp[cc] = vc;
-                        xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
-                        xp[cc] = xs[cc];
+                __syncwarp();
+                if (lane == 0) {
+                    // release the slot; the last warp refills it with position pos + kBS
+                    __threadfence_block();
+                    if (atomicAdd(&s_rel[slot], 1u) == NT / 32 - 1) {
+                        s_rel[slot] = 0;
+                        __threadfence_block();
+                        fence_proxy_async_shared();
+                        if (q + kBS < ntl) issue(pos + kBS, src + (int64_t)(q + kBS) * f4_per_tile);
                     }
-                    pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
                 }
             }
+        }
+        kk += ntl;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = lo + r * NT + tid;
+            if (i < hi) {
+                const float acc[3] = {a.G * (tot[r].x.x + tot[r].x.y), a.G * (tot[r].y.x + tot[r].y.y),
+                                      a.G * (tot[r].z.x + tot[r].z.y)};
+                float *xp = a.x + 3 * (b0 + i);
+                float *vp = a.v + 3 * (b0 + i);
+                float xs[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                    vp[cc] = vc;
+                    xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
+                    xp[cc] = xs[cc];
+                }
+                pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
+            }
+        }
+    };
+
+    for (;;) {
+        if (tid == 0) {
+            bool abort;
+            const unsigned id = pick(abort);
+            s_item = id;
+            s_abort = abort ? 1 : 0;
+            if (id < total && !abort && !give_up) {
+                // the ring is free (the previous item ended with a barrier):
+                // start streaming this item's first tiles before the broadcast
+                const int t = (int)(id / (unsigned)a.items_per_step);
+                const int sys = a.item_sys[id % (unsigned)a.items_per_step];
+                const int64_t n = a.off[sys + 1] - a.off[sys];
+                const int ntl = (int)((n + a.jt - 1) / a.jt);
+                const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + a.poff[sys];
+                fence_proxy_async_global();
+                for (int q = 0; q < ntl && q < kBS; ++q) issue(kk + q, src + (int64_t)q * f4_per_tile);
+            }
+        }
+        __syncthreads();
+        const unsigned id = s_item;
+        if (id >= total) break;
+        const int t = (int)(id / (unsigned)a.items_per_step);
+        const int k = (int)(id % (unsigned)a.items_per_step);
+        const int s = a.item_sys[k];
+        const int r = a.item_r[k];
+        const int64_t lo = a.item_lo[k];
+        const int64_t b0 = a.off[s];
+        const int64_t n = a.off[s + 1] - b0;
+        const int64_t p0 = a.poff[s];
+        const int ntl = (int)((n + a.jt - 1) / a.jt);
+        const int64_t hi = lo + (int64_t)NT * r < n ? lo + (int64_t)NT * r : n;
+        const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
+        float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
+        if (!s_abort && !give_up) {
+            if constexpr (RMAX >= 8) {
+                if (r == 8) run_item(std::integral_constant<int, 8>{}, src, dst, b0, lo, hi, ntl);
+            }
+            if constexpr (RMAX >= 4) {
+                if (r == 4) run_item(std::integral_constant<int, 4>{}, src, dst, b0, lo, hi, ntl);
+            }
+            if constexpr (RMAX >= 2) {
+                if (r == 2) run_item(std::integral_constant<int, 2>{}, src, dst, b0, lo, hi, ntl);
+            }
+            if (r == 1) run_item(std::integral_constant<int, 1>{}, src, dst, b0, lo, hi, ntl);
             fence_proxy_async_global();
         }
         __syncthreads();
@@ -218,8 +325,10 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 2)) batched_kernel(const Bat
             atomicAdd(a.done + s, 1u);  // release this item to step t+1
         }
     }
-    // never leave while our own copies may still be landing
+    // never leave while our own copies may still be landing (the loop above
+    // ended with a __syncthreads, so every issue is visible in s_issued)
     if (tid == 0) {
+        const uint32_t issued = s_issued;
         for (uint32_t q = issued > (uint32_t)kBS ? issued - kBS : 0; q < issued; ++q) {
             if (!mbar_wait(&full[q % kBS], (q / kBS) & 1, kDrainTimeoutNs))
                 atomicOr(a.err, kErrDrain);
@@ -259,14 +368,32 @@ __global__ void batched_fill_kernel(const int64_t *off, float *x, float *v, floa
     }
 }
 
-template <int NT, int R>
-size_t batched_smem(int jt) {
-    return 128 + (size_t)kBS * jt * 16;
+size_t batched_smem(int jt) { return 128 + (size_t)kBS * jt * 16; }
+
+using BatchedFn = void (*)(const BatchArgs);
+
+// Shapes of the ensemble kernel: (threads, largest R). Up to R = 2 the
+// registers fit 512 resident threads per SM; the 512-thread forms then run
+// one CTA per SM.
+BatchedFn batched_fn(int nt, int rmax) {
+    switch (nt * 16 + rmax) {
+        case 128 * 16 + 1: return batched_kernel<128, 1>;
+        case 128 * 16 + 2: return batched_kernel<128, 2>;
+        case 128 * 16 + 4: return batched_kernel<128, 4>;
+        case 128 * 16 + 8: return batched_kernel<128, 8>;
+        case 256 * 16 + 1: return batched_kernel<256, 1>;
+        case 256 * 16 + 2: return batched_kernel<256, 2>;
+        case 256 * 16 + 4: return batched_kernel<256, 4>;
+        case 256 * 16 + 8: return batched_kernel<256, 8>;
+        case 512 * 16 + 1: return batched_kernel<512, 1>;
+        case 512 * 16 + 2: return batched_kernel<512, 2>;
+        default: return nullptr;
+    }
 }
 
 // Device copy of the plan inside the scratch block.
 struct Layout {
-    size_t o_off, o_poff, o_isys, o_ichunk, o_nch, o_next, o_done, o_xm0, o_xm1, total;
+    size_t o_off, o_poff, o_isys, o_ilo, o_ir, o_nit, o_next, o_done, o_xm0, o_xm1, total;
 };
 
 Layout layout_of(const BatchPlan &p) {
@@ -280,8 +407,9 @@ Layout layout_of(const BatchPlan &p) {
     L.o_off = take(p.off.size() * 8);
     L.o_poff = take(p.poff.size() * 8);
     L.o_isys = take(p.item_sys.size() * 4);
-    L.o_ichunk = take(p.item_chunk.size() * 4);
-    L.o_nch = take(p.nchunks.size() * 4);
+    L.o_ilo = take(p.item_lo.size() * 4);
+    L.o_ir = take(p.item_r.size() * 4);
+    L.o_nit = take(p.nitems.size() * 4);
     L.o_next = take(4);                            // queue head ...
     L.o_done = take((size_t)p.nsys * 4);          // ... and completion counters: zeroed per launch
     L.o_xm0 = take((size_t)p.total_pad * 16);
@@ -298,52 +426,65 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
                   std::string &why) {
     (void)device;
     p.nsys = (int)off.size() - 1;
-    if (p.nt == 0) p.nt = 128;
-    if (p.r == 0) p.r = 2;
+    if (p.nt == 0) p.nt = 256;  // one CTA per SM: no co-resident CTA starves another
+    if (p.r == 0) p.r = 8;
     if (p.jt == 0) p.jt = 64;
-    if (p.nt != 128 || (p.r != 1 && p.r != 2 && p.r != 4) || p.jt % 2 || kPadBodies % p.jt) {
+    const BatchedFn fn = batched_fn(p.nt, p.r);
+    if (!fn || p.jt % 2 || kPadBodies % p.jt) {
         why = "unsupported batched shape";
         return false;
     }
     int occ = 0;
-    cudaError_t e;
-    const size_t smem = batched_smem<128, 2>(p.jt);
-    if (p.r == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 1>, 128, smem);
-    else if (p.r == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 2>, 128, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<128, 4>, 128, smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem(p.jt));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p.nt, batched_smem(p.jt));
     if (e != cudaSuccess || occ <= 0) {
         why = "occupancy query failed";
         return false;
     }
     p.off = off;
     p.poff.assign(p.nsys, 0);
-    p.nchunks.assign(p.nsys, 0);
+    p.nitems.assign(p.nsys, 0);
     p.total = off[p.nsys];
-    const int64_t chunk = (int64_t)p.nt * p.r;
+    // Items of a system: full chunks of NT x rmax i-bodies, then the ragged
+    // rest as power-of-two items (3 and 7 rows of NT round up to 4 and 8), so
+    // that no item computes more than NT - 1 idle i-slots.
+    struct Item { int sys, lo, r, ntl; };
+    std::vector<Item> items;
     int64_t acc = 0;
     for (int s = 0; s < p.nsys; ++s) {
         const int64_t n = off[s + 1] - off[s];
         p.poff[s] = acc;
         acc += (n + p.jt - 1) / p.jt * p.jt;
-        p.nchunks[s] = (int)((n + chunk - 1) / chunk);
+        const int ntl = (int)((n + p.jt - 1) / p.jt);
+        int64_t lo = 0;
+        const int64_t full = (int64_t)p.nt * p.r;
+        for (; lo + full <= n; lo += full) items.push_back({s, (int)lo, p.r, ntl});
+        int rows = (int)((n - lo + p.nt - 1) / p.nt);
+        if (rows == 3 || rows == 7) rows += 1;
+        for (int r = p.r; r >= 1 && rows > 0; r >>= 1)
+            if (rows >= r) {
+                items.push_back({s, (int)lo, r, ntl});
+                lo += (int64_t)r * p.nt;
+                rows -= r;
+            }
     }
+    for (int s = 0; s < p.nsys; ++s) p.nitems[s] = 0;
+    for (const Item &it : items) p.nitems[it.sys]++;
     p.total_pad = std::max<int64_t>(acc, p.jt);
-    // items of one step: largest systems first, chunks in order
-    std::vector<int> order(p.nsys);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return off[a + 1] - off[a] > off[b + 1] - off[b];
+    // items of one step: most work first (R x tiles), then by system and row
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+        return (int64_t)x.r * x.ntl > (int64_t)y.r * y.ntl;
     });
     p.item_sys.clear();
-    p.item_chunk.clear();
-    for (int s : order)
-        for (int c = 0; c < p.nchunks[s]; ++c) {
-            p.item_sys.push_back(s);
-            p.item_chunk.push_back(c);
-        }
+    p.item_lo.clear();
+    p.item_r.clear();
+    for (const Item &it : items) {
+        p.item_sys.push_back(it.sys);
+        p.item_lo.push_back(it.lo);
+        p.item_r.push_back(it.r);
+    }
     p.items_per_step = (int)p.item_sys.size();
     p.ncta = std::max(1, std::min(occ * num_sms, std::max(p.items_per_step, 1)));
     Layout L = layout_of(p);
@@ -378,8 +519,9 @@ cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
     NB_UP(off, L.o_off)
     NB_UP(poff, L.o_poff)
     NB_UP(item_sys, L.o_isys)
-    NB_UP(item_chunk, L.o_ichunk)
-    NB_UP(nchunks, L.o_nch)
+    NB_UP(item_lo, L.o_ilo)
+    NB_UP(item_r, L.o_ir)
+    NB_UP(nitems, L.o_nit)
 #undef NB_UP
     return cudaSuccess;
 }
@@ -403,8 +545,9 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     a.off = (const int64_t *)(b + L.o_off);
     a.poff = (const int64_t *)(b + L.o_poff);
     a.item_sys = (const int *)(b + L.o_isys);
-    a.item_chunk = (const int *)(b + L.o_ichunk);
-    a.nchunks = (const int *)(b + L.o_nch);
+    a.item_lo = (const int *)(b + L.o_ilo);
+    a.item_r = (const int *)(b + L.o_ir);
+    a.nitems = (const int *)(b + L.o_nit);
     a.next = (unsigned *)(b + L.o_next);
     a.done = (unsigned *)(b + L.o_done);
     a.xm0 = (float4 *)(b + L.o_xm0);
@@ -428,16 +571,16 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3((unsigned)p.ncta);
     cfg.blockDim = dim3((unsigned)p.nt);
-    cfg.dynamicSmemBytes = batched_smem<128, 2>(p.jt);
+    cfg.dynamicSmemBytes = batched_smem(p.jt);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (p.r == 1) return cudaLaunchKernelEx(&cfg, batched_kernel<128, 1>, a);
-    if (p.r == 2) return cudaLaunchKernelEx(&cfg, batched_kernel<128, 2>, a);
-    return cudaLaunchKernelEx(&cfg, batched_kernel<128, 4>, a);
+    BatchedFn fn = batched_fn(p.nt, p.r);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 }  // namespace nb

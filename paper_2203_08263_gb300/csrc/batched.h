@@ -9,21 +9,24 @@
 namespace nb {
 
 // Host-side plan of the persistent ensemble kernel. The work of one step is
-// split into items (system s, i-chunk c) of at most NT x R i-bodies each,
-// against all of the system's j-bodies. Items are numbered step-major (all
-// items of step t before those of step t+1) and, within a step, by
-// decreasing system size. Persistent CTAs pop item numbers from one atomic
-// counter; an item of step t waits only until every item of step t-1 of the
-// same system is done (always lower numbers, so the oldest unfinished item
-// can always run).
+// split into items (system s, first i-body lo, R) of NT x R i-bodies each,
+// against all of the system's j-bodies: full items use R = r (the plan's
+// largest), the ragged rest of a system smaller powers of two. Items are
+// numbered step-major (all items of step t before those of step t+1) and,
+// within a step, by decreasing work. Persistent CTAs pop item numbers from
+// one atomic counter; an item of step t waits only until every item of step
+// t-1 of the same system is done (always lower numbers, so the oldest
+// unfinished item can always run).
 struct BatchPlan {
     int nsys = 0;
-    int nt = 128, r = 2, jt = 64;   // kernel shape
+    int nt = 256, r = 8, jt = 64;   // kernel shape: threads, largest R, j-tile
     int ncta = 0;                   // persistent grid (resident CTAs)
     int items_per_step = 0;
+    int origin = 0;                 // 0 default shape, 1 autotuned, 2 set by the caller
     int64_t total = 0, total_pad = 0;
     std::vector<int64_t> off, poff;  // body offsets, packed offsets (per system)
-    std::vector<int> item_sys, item_chunk, nchunks;
+    std::vector<int> item_sys, item_lo, item_r;  // per item of one step
+    std::vector<int> nitems;                     // items per step of each system
     size_t scratch_bytes = 0;   // plan + counters + two packed buffers
     uint64_t signature = 0;     // hash of sizes and shape
     int64_t launches = 3;       // memset, pack, persistent kernel

@@ -47,6 +47,7 @@ SIGNATURES = {
     "nb_batched_max_n": (_i64, []),
     "nb_autotune_batched": (_i, [_vp, _i, _vp]),
     "nb_get_batched_config": (_i, [_vp, _i, _vp, _c.POINTER(_i)]),
+    "nb_set_batched_config": (_i, [_vp, _i, _vp, _i, _i, _i]),
     "nb_adjoint": (_i, [_vp, _i64, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_vjp": (_i, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_energy": (_i, [_vp, _i64, _vp, _vp, _vp, _c.POINTER(_d), _vp]),
@@ -202,7 +203,13 @@ class Context:
         self._check(self.lib.nb_get_batched_config(self.h, int(offsets.shape[0]) - 1, _ptr(offsets), out),
                     "nb_get_batched_config")
         return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "items_per_step": out[3],
-                "ctas": out[4], "tuned": bool(out[5])}
+                "ctas": out[4], "tuned": out[5] == 1, "pinned": out[5] == 2}
+
+    def set_batched_config(self, offsets, threads: int, bodies_per_thread: int, jtile: int):
+        """Pin the batched shape for these sizes; (0, 0, 0) returns to the default."""
+        self._check(self.lib.nb_set_batched_config(self.h, int(offsets.shape[0]) - 1, _ptr(offsets),
+                                                   int(threads), int(bodies_per_thread), int(jtile)),
+                    "nb_set_batched_config")
 
     # ---- reverse
     def vjp(self, x, m, abar, stream=None):

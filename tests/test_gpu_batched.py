@@ -66,7 +66,8 @@ def test_autotuned_batched_shape(nbm):
     assert not ctx.get_batched_config(offt)["tuned"]
     ctx.autotune_batched(offt)
     cfg = ctx.get_batched_config(offt)
-    assert cfg["tuned"] and cfg["bodies_per_thread"] in (1, 2, 4) and cfg["jtile"] in (64, 128)
+    assert cfg["tuned"] and cfg["threads"] in (128, 256, 512)
+    assert cfg["bodies_per_thread"] in (1, 2, 4, 8) and cfg["jtile"] in (64, 128)
     xt = torch.tensor(x, dtype=torch.float32, device=DEV)
     vt = torch.tensor(v, dtype=torch.float32, device=DEV)
     mt = torch.tensor(m, dtype=torch.float32, device=DEV)
@@ -94,3 +95,47 @@ def test_c4_full_ensemble_sampled(nbm):
         err = rel_l2(gx[a:b], xr)
         print(f"C4 system {s} (N={b - a}): x rel L2 {err:.2e}")
         assert err <= 1e-4
+
+
+# Sizes whose ragged rests need every item kind: rows of 128 i-bodies of
+# 1..8 (3 and 7 rounded up), a full chunk of 8 rows plus a rest, and tiny ones.
+TAIL_SIZES = [1, 127, 128, 129, 300, 385, 640, 700, 896, 1000, 1024, 1025, 1500, 2047, 2200, 3]
+
+
+@pytest.mark.parametrize("nt,r,jt", [(128, 1, 64), (128, 2, 128), (128, 4, 64), (128, 8, 64), (128, 8, 32),
+                                     (256, 1, 64), (256, 4, 256), (256, 8, 128), (512, 1, 128),
+                                     (512, 2, 64)])
+def test_pinned_shapes_every_item_kind(nbm, nt, r, jt):
+    sizes = TAIL_SIZES
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rng = np.random.default_rng(100 + nt + r + jt)
+    x = rng.uniform(-1, 1, (off[-1], 3))
+    v = rng.uniform(-0.1, 0.1, (off[-1], 3))
+    m = rng.uniform(0.5, 1.5, off[-1]) / 1000
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    offt = torch.tensor(off, dtype=torch.int64)
+    ctx.set_batched_config(offt, nt, r, jt)
+    cfg = ctx.get_batched_config(offt)
+    assert cfg["pinned"] and (cfg["threads"], cfg["bodies_per_thread"], cfg["jtile"]) == (nt, r, jt)
+    xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float32, device=DEV)
+    ctx.run_batched(offt, xt, vt, mt, 3)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 3)
+        assert rel_l2(gx[a:b], xr) <= 1e-5, (s, sizes[s])
+        assert rel_l2(gv[a:b], vr) <= 1e-4, (s, sizes[s])
+    ctx.set_batched_config(offt, 0, 0, 0)
+    assert not ctx.get_batched_config(offt)["pinned"]
+
+
+def test_set_batched_config_rejects_bad_shapes(nbm):
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    offt = torch.tensor([0, 100, 300], dtype=torch.int64)
+    for nt, r, jt in ((128, 3, 64), (128, 16, 64), (128, 8, 48), (128, 8, 512), (128, 0, 64),
+                      (512, 4, 64), (64, 1, 64), (0, 0, 64)):
+        with pytest.raises(RuntimeError):
+            ctx.set_batched_config(offt, nt, r, jt)
