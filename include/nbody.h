@@ -117,12 +117,16 @@ nb_status nb_accel(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a
 nb_status nb_step(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, void *stream);
 
 /*
- * `steps` steps in place on x, v, replayed from a CUDA graph that the context
- * captures once per (n, buffers, steps, checkpoint layout) and caches.
- * ckpt (nullable, device): [steps/ckpt_every + 1][n][6] in the state type;
- * slot k receives (x, v) after k*ckpt_every steps (slot 0 = the input state).
- * ckpt_every must divide steps when ckpt != NULL. The paper scheme only when
- * checkpointing.
+ * `steps` steps in place on x, v (Section 3.1's loop over the update), by one
+ * of two paths with the same arithmetic: a CUDA graph of one force launch per
+ * step that the context captures once per (n, buffers, steps, checkpoint
+ * layout) and caches; or, for FP32 systems of at most 4096 bodies, one
+ * kernel on one thread-block cluster that keeps the positions in distributed
+ * shared memory across all steps. nb_autotune picks the faster path per size;
+ * untuned, the cluster path serves n <= 512. ckpt (nullable, device):
+ * [steps/ckpt_every + 1][n][6] in the state type; slot k receives (x, v)
+ * after k*ckpt_every steps (slot 0 = the input state). ckpt_every must divide
+ * steps when ckpt != NULL. The paper scheme only when checkpointing.
  */
 nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
                  void *ckpt, int ckpt_every, void *stream);
@@ -208,7 +212,9 @@ nb_status nb_energy(nb_ctx *ctx, int64_t n, const void *x, const void *v, const 
 /*
  * Time the candidate kernel shapes for problems of size n in mode `mode`
  * (0 = forward, 1 = adjoint VJP) and store the fastest in the context's
- * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). Calls
+ * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). In
+ * mode 0 with FP32 state and n <= 4096 it also times nb_run's two paths
+ * (graph of force launches, one-cluster kernel) and records the faster. Calls
  * that find no entry for their size bucket use a built-in heuristic instead.
  * Synchronous.
  */
@@ -241,7 +247,11 @@ typedef enum {
      * paper's math-operation experiment, Sections 3.2.6 and 3.3.6):
      * 0 = MUFU rsqrt cubed (default), 1 = IEEE sqrt then division,
      * 2 = powf(s, -1.5). Tuned shapes apply to 0 only. */
-    NB_DBG_MATH_VARIANT = 3
+    NB_DBG_MATH_VARIANT = 3,
+    /* nb_run path: 0 = chosen per size (default), 1 = graph of force
+     * launches, 2 = one-cluster kernel (NB_ERR_UNSUPPORTED at nb_run when
+     * the system does not qualify). */
+    NB_DBG_RUN_PATH = 4
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 

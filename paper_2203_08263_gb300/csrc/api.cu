@@ -243,6 +243,11 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         clear_graphs(ctx);
         return NB_OK;
     }
+    if (key == NB_DBG_RUN_PATH) {
+        if (value < 0 || value > 2) return fail(ctx, NB_ERR_INVALID, "run path must be 0, 1 or 2");
+        ctx->run_path = (int)value;
+        return NB_OK;
+    }
     if (key == NB_DBG_STALL_PRODUCER) {
         if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
         ctx->debug = value ? (ctx->debug | kDbgStallProducer) : (ctx->debug & ~kDbgStallProducer);

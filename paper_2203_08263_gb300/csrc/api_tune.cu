@@ -95,6 +95,42 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     NB_TRY(sync_and_check(ctx, st));
     ctx->tuned[tune_key(ctx, mode, n)] = best;
     clear_graphs(ctx);
+    // nb_run's two paths for small FP32 systems: the graph of force launches
+    // (with the shape just chosen) against the one-cluster kernel, 20 steps
+    // each on zeroed state (timing does not depend on the values)
+    int cluster = 0;
+    if (mode == 0 && !f64_state(ctx) && ctx->math == 0 && n <= kClusterMaxN) cluster = cluster_run_size(n);
+    if (cluster) {
+        float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[4].p, *m = (float *)ctx->tune[3].p;
+        NB_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 12, st));
+        NB_CUDA(cudaMemsetAsync(v, 0, (size_t)n * 12, st));
+        NB_CUDA(cudaMemsetAsync(m, 0, (size_t)n * 4, st));
+        const int steps = 20;
+        const int saved_path = ctx->run_path;
+        float ms_path[2] = {1e30f, 1e30f};
+        nb_status rs = NB_OK;
+        for (int path = 1; path <= 2 && rs == NB_OK; ++path) {
+            ctx->run_path = path;
+            rs = run_device(ctx, n, x, v, m, steps, nullptr, 0, st);  // warm-up (and graph capture)
+            for (int rep = 0; rs == NB_OK && rep < 3; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) { rs = NB_ERR_CUDA; break; }
+                rs = run_device(ctx, n, x, v, m, steps, nullptr, 0, st);
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rs = NB_ERR_CUDA;
+                    break;
+                }
+                float t = 0;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms_path[path - 1] = std::min(ms_path[path - 1], t);
+            }
+        }
+        ctx->run_path = saved_path;
+        NB_TRY(rs);
+        NB_TRY(sync_and_check(ctx, st));
+        ctx->tuned[tune_key(ctx, mode, n) + "|run"] =
+            TuneEntry{ms_path[1] < ms_path[0] ? 1 : 0, cluster, 0, 0, 0};
+        clear_graphs(ctx);
+    }
     save_tune_file(ctx);
     return NB_OK;
 }

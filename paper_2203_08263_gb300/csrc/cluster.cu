@@ -1,0 +1,273 @@
+// Small systems: every step of nb_run in one launch of one thread-block
+// cluster. The force sum (Eq. 1 with softening, as the single-system kernel)
+// and the printed update (half kick v += a dt/2, drift x += v dt with the new
+// v; or the kick-drift-kick variant) are the same arithmetic as the graph
+// path; what differs is where the state lives between steps. Each CTA of the
+// cluster keeps a full replica of the packed positions in its shared memory
+// (two buffers), owns a contiguous slice of the bodies and keeps their x and v
+// in registers. Per step it sums the forces on its slice against its own
+// replica, updates the slice, writes the slice's new packed records into the
+// other buffer of every CTA through distributed shared memory, and meets the
+// others at one cluster barrier. No global memory is touched between the
+// first load and the final store (checkpoints aside), and no kernel boundary
+// separates the steps: at N of a few thousand the graph path's per-step
+// launch, bulk-copy and split-reduction latencies dominate, and this path
+// removes them.
+#include <cstring>
+
+#include "kernels.h"
+#include "engine.cuh"
+
+namespace nb {
+
+namespace {
+
+struct ClusterArgs {
+    int n, npad, slice;  // bodies, cluster size x slice, bodies per CTA (even)
+    int steps, kdk;      // paper steps; 1: kick-drift-kick scheme
+    float eps2, G, dt;
+    float *x, *v;        // [n][3], updated in place
+    const float *m;      // [n]
+    float *ckpt;         // nullable: slots of [n][6] (x, v), slot s after step s * ckpt_every
+    int ckpt_every;
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t smem, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_f4(uint32_t addr, float4 v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Every thread of every CTA of the cluster arrives (release) and waits
+// (acquire): remote shared-memory stores before it are visible after it.
+__device__ __forceinline__ void cluster_barrier() {
+    __syncwarp();  // the .aligned form wants the whole warp converged here
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+// Threads per body in the force sum: the largest power of two Q <= 32 with
+// slice x Q <= NT (the Q lanes of a body split its j-pairs and are reduced
+// with shuffles).
+template <int NT>
+__device__ __forceinline__ int lanes_per_body(int slice) {
+    int q = 1;
+    while (q < 32 && slice * q * 2 <= NT) q *= 2;
+    return q;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a) {
+    extern __shared__ __align__(16) float4 rep[];  // [2][npad] packed pair records
+    const int tid = threadIdx.x;
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t csize = cluster_nctarank();
+    const int S = a.slice;
+    const int npad = a.npad;
+    const int Q = lanes_per_body<NT>(S);
+    const int il = tid / Q, jq = tid % Q;
+    const bool active = il < S;                    // sums forces for body i
+    const int i = (int)rank * S + (active ? il : 0);
+    const bool owner = active && jq == 0 && i < a.n;  // updates body i
+
+    // both replicas: every body's record in buffer 0, zeros in buffer 1
+    for (int k = tid; k < npad; k += NT) {
+        if (k < a.n)
+            pair_put(rep, k, a.x[3 * k], a.x[3 * k + 1], a.x[3 * k + 2], a.m[k]);
+        else
+            pair_put(rep, k, 0.f, 0.f, 0.f, 0.f);
+        pair_put(rep + npad, k, 0.f, 0.f, 0.f, 0.f);
+    }
+    float xs[3] = {0.f, 0.f, 0.f}, vs[3] = {0.f, 0.f, 0.f}, mi = 0.f;
+    if (owner) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xs[c] = a.x[3 * i + c];
+            vs[c] = a.v[3 * i + c];
+        }
+        mi = a.m[i];
+        if (a.ckpt) {
+            float *ck = a.ckpt + 6 * (int64_t)i;
+            ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
+            ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
+        }
+    }
+    // no CTA writes into another's buffer 1 before that one has zeroed it
+    cluster_barrier();
+
+    const float dt = a.dt;
+    const int evals = a.steps + (a.kdk && a.steps > 0 ? 1 : 0);
+    int cur = 0;
+    for (int t = 0; t < evals; ++t) {
+        const float4 *src = rep + cur * npad;
+        float4 *dst = rep + (cur ^ 1) * npad;
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        if (active) {
+            AccelF32x2::I ist;
+            AccelF32x2::T tot;
+            AccelF32x2::C cst;
+            cst.eps2 = dup(a.eps2);
+            ist.nx = dup(-pair_get(src, i, 0));
+            ist.ny = dup(-pair_get(src, i, 1));
+            ist.nz = dup(-pair_get(src, i, 2));
+            AccelF32x2::zero_total(tot);
+            const int npairs = npad >> 1;
+#pragma unroll 4
+            for (int p = jq; p < npairs; p += Q) {
+                const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
+                AccelF32x2::interact(rec, ist, tot, cst);
+            }
+            ax = tot.x.x + tot.x.y;
+            ay = tot.y.x + tot.y.y;
+            az = tot.z.x + tot.z.y;
+        }
+        for (int off = Q >> 1; off > 0; off >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, off);
+            ay += __shfl_xor_sync(0xffffffffu, ay, off);
+            az += __shfl_xor_sync(0xffffffffu, az, off);
+        }
+        const bool last_kick = a.kdk && t == a.steps;  // the closing half kick of KDK
+        if (owner) {
+            const float acc[3] = {a.G * ax, a.G * ay, a.G * az};
+            const bool double_kick = a.kdk && t > 0 && !last_kick;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                // v <- v + a*dt/2 (twice between two drifts of the KDK scheme), then x += v*dt
+                float vc = __fadd_rn(vs[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
+                if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
+                vs[c] = vc;
+                if (!last_kick) xs[c] = __fadd_rn(xs[c], __fmul_rn(vc, dt));
+            }
+            if (!last_kick) {
+                pair_put(dst, i, xs[0], xs[1], xs[2], mi);
+                if (a.ckpt && (t + 1) % a.ckpt_every == 0) {
+                    float *ck = a.ckpt + (int64_t)((t + 1) / a.ckpt_every) * 6 * a.n + 6 * (int64_t)i;
+                    ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
+                    ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
+                }
+            }
+        }
+        if (last_kick) break;
+        __syncthreads();  // this CTA's slice of dst is complete
+        // The slice of S bodies is float4 [rank*S, rank*S + S) of the pair
+        // layout (S even): copy it into the same place of every other CTA.
+        const int base = (int)rank * S;
+        for (int q = tid; q < (int)(csize - 1) * S; q += NT) {
+            const uint32_t to = (rank + 1 + (uint32_t)(q / S)) % csize;
+            const int k = base + q % S;
+            st_cluster_f4(map_to_rank(smem_addr(&dst[k]), to), dst[k]);
+        }
+        cluster_barrier();
+        cur ^= 1;
+    }
+    if (owner) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.x[3 * i + c] = xs[c];
+            a.v[3 * i + c] = vs[c];
+        }
+    }
+}
+
+constexpr int kClusterThreads = 512;
+
+}  // namespace
+
+// Largest cluster this device can run the kernel with for n bodies (16 if
+// non-portable clusters are allowed and fit, else 8), 0 if none: the two
+// replicas must fit in shared memory.
+int cluster_run_size(int64_t n) {
+    if (n <= 0 || n > kClusterMaxN) return 0;
+    auto fn = cluster_run_kernel<kClusterThreads>;
+    for (int c : {16, 8}) {
+        const int64_t slice = ((n + c - 1) / c + 1) / 2 * 2;
+        if (slice > kClusterThreads) continue;
+        const size_t smem = (size_t)2 * c * slice * 16;
+        if (smem > 200 * 1024) continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            continue;
+        if (c > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            continue;
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) == cudaSuccess && clusters > 0) return c;
+        cudaGetLastError();  // clear a refused query
+    }
+    cudaGetLastError();
+    return 0;
+}
+
+cudaError_t launch_cluster_run(int cluster, int64_t n, float *x, float *v, const float *m, int steps,
+                               int kdk, float eps2, float G, float dt, float *ckpt, int ckpt_every,
+                               cudaStream_t st) {
+    if (cluster <= 0 || n <= 0 || n > kClusterMaxN) return cudaErrorInvalidValue;
+    auto fn = cluster_run_kernel<kClusterThreads>;
+    ClusterArgs a;
+    a.n = (int)n;
+    a.slice = (int)(((n + cluster - 1) / cluster + 1) / 2 * 2);
+    a.npad = cluster * a.slice;
+    a.steps = steps;
+    a.kdk = kdk;
+    a.eps2 = eps2;
+    a.G = G;
+    a.dt = dt;
+    a.x = x;
+    a.v = v;
+    a.m = m;
+    a.ckpt = ckpt;
+    a.ckpt_every = ckpt_every > 0 ? ckpt_every : 1;
+    const size_t smem = (size_t)2 * a.npad * 16;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cluster > 8) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)cluster);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+}  // namespace nb

@@ -317,8 +317,49 @@ void graph_insert(nb_ctx *ctx, const std::string &key, cudaGraphExec_t ex, int64
 
 // ------------------------------------------------------- device run path
 
+nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
+    *cluster = 0;
+    if (ctx->run_path == 1) return NB_OK;
+    int c = 0;
+    if (!f64_state(ctx) && ctx->math == 0 && n <= kClusterMaxN) {
+        auto it = ctx->cluster_sizes.find(n);
+        if (it == ctx->cluster_sizes.end()) {
+            c = cluster_run_size(n);
+            ctx->cluster_sizes[n] = c;
+        } else {
+            c = it->second;
+        }
+    }
+    if (ctx->run_path == 2) {
+        if (!c)
+            return fail(ctx, NB_ERR_UNSUPPORTED,
+                        "the one-cluster path runs FP32 systems of at most %lld bodies (MUFU "
+                        "denominator) that fit a cluster on this device",
+                        (long long)kClusterMaxN);
+        *cluster = c;
+        return NB_OK;
+    }
+    if (!c) return NB_OK;
+    auto t = ctx->tuned.find(tune_key(ctx, 0, n) + "|run");
+    if (t != ctx->tuned.end())
+        *cluster = t->second.pol ? c : 0;
+    else
+        *cluster = n <= kClusterDefaultN ? c : 0;
+    return NB_OK;
+}
+
 nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
                      void *ckpt, int ckpt_every, cudaStream_t st) {
+    int cluster = 0;
+    NB_TRY(choose_run_path(ctx, n, &cluster));
+    if (cluster) {
+        NB_CUDA(launch_cluster_run(cluster, n, (float *)x, (float *)v, (const float *)m, steps,
+                                   ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0,
+                                   (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
+                                   (float)ctx->p.dt, (float *)ckpt, ckpt_every, st));
+        ctx->launches += 1;
+        return NB_OK;
+    }
     Shape s;
     NB_TRY(choose_shape(ctx, 0, n, &s, nullptr));
     Plan p;

@@ -52,6 +52,8 @@ struct nb_ctx {
     uint64_t timeout_ns = 2000000000ull;
     int debug = 0;
     int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
+    int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one-cluster kernel
+    std::map<int64_t, int> cluster_sizes;  // n -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;
     std::map<uint64_t, nb::BatchPlan> batched_tuned;  // size profile -> tuned batched shape
@@ -121,6 +123,9 @@ nb_status pack(nb_ctx *ctx, int64_t n, int64_t npad, const void *x, const void *
                float4 *xm, void *ckpt0, cudaStream_t st);
 GraphEntry *graph_lookup(nb_ctx *ctx, const std::string &key);
 void graph_insert(nb_ctx *ctx, const std::string &key, cudaGraphExec_t ex, int64_t nodes);
+// Which nb_run path serves n bodies: *cluster = the cluster size of the
+// one-cluster kernel, or 0 for the graph of force launches.
+nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster);
 nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
                      void *ckpt, int ckpt_every, cudaStream_t st);
 nb_status accel_device(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a_out,

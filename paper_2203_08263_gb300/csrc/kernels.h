@@ -67,4 +67,20 @@ cudaError_t launch_copy_ckpt_state(int64_t n, int f64, const void *ckpt_slot, vo
 // FP32 FFMA / f32x2 FMA TFLOP/s and MUFU rsqrt Gop/s micro-benchmarks
 cudaError_t measure_peaks(int blocks, float *sink, cudaStream_t st, double out[3]);
 
+// Small systems in one cluster launch (csrc/cluster.cu): every step of a run
+// in one kernel, positions replicated in the shared memory of each CTA of one
+// thread-block cluster and exchanged through distributed shared memory.
+constexpr int64_t kClusterMaxN = 4096;      // two replicas of 64 KiB
+// Untuned, the cluster path serves systems up to this size: measured on
+// GB300 at 100 steps, 1.9 vs 5.2 us per step at N = 256 and 3.5 vs 5.7 at
+// N = 512, but 9.7 vs 7.4 at N = 1024, where the graph path's 152 SMs outrun
+// one cluster's 16.
+constexpr int64_t kClusterDefaultN = 512;
+// Cluster size (16, or 8 where 16 cannot be scheduled) for n bodies; 0 if
+// the path cannot run n bodies on this device.
+int cluster_run_size(int64_t n);
+cudaError_t launch_cluster_run(int cluster, int64_t n, float *x, float *v, const float *m, int steps,
+                               int kdk, float eps2, float G, float dt, float *ckpt, int ckpt_every,
+                               cudaStream_t st);
+
 }  // namespace nb

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnbody.so")
 NB_OK, NB_ERR_INVALID, NB_ERR_CUDA, NB_ERR_NOMEM, NB_ERR_TIMEOUT, NB_ERR_UNSUPPORTED = range(6)
 NB_FP32, NB_FP32_COMP_FP64_STATE = 0, 1
 NB_SCHEME_PAPER, NB_SCHEME_KDK = 0, 1
-NB_DBG_WAIT_TIMEOUT_NS, NB_DBG_STALL_PRODUCER, NB_DBG_MATH_VARIANT = 1, 2, 3
+NB_DBG_WAIT_TIMEOUT_NS, NB_DBG_STALL_PRODUCER, NB_DBG_MATH_VARIANT, NB_DBG_RUN_PATH = 1, 2, 3, 4
 MODE_FORWARD, MODE_ADJOINT, MODE_POTENTIAL = 0, 1, 2
 
 # Every symbol include/nbody.h declares, with (restype, argtypes).

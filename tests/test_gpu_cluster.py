@@ -1,0 +1,119 @@
+"""GPU parity of nb_run's one-cluster path (positions in distributed shared
+memory, every step in one kernel) against the FP64 oracle and against the
+graph-of-launches path, through the C-ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_08263_gb300 import ics
+from gpu_util import ensure_built, rel_l2, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GRAPH, CLUSTER = 1, 2
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    ensure_built()
+    from paper_2203_08263_gb300 import nbody
+    return nbody
+
+
+def _t(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _ctx(nbm, path, G=1.0, eps=0.01, dt=1e-3, scheme="paper"):
+    ctx = nbm.Context(G, eps, dt, scheme=scheme)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, path)
+    return ctx
+
+
+# odd sizes, slices that do not divide evenly, one body, and the path's limit
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 255, 256, 1000, 1024, 2047, 3001, 4096])
+def test_cluster_run_matches_oracle(nbm, n):
+    s = ics.cube(n, seed=500 + n)
+    steps = 10
+    ctx = _ctx(nbm, CLUSTER)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    before = ctx.launch_count
+    ctx.run(x, v, m, steps)
+    ctx.sync()
+    assert ctx.launch_count - before == 1  # all steps in one kernel
+    xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, steps)
+    assert rel_l2(to_np(x), xr) <= 1e-5
+    assert rel_l2(to_np(v), vr) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [64, 1500])
+def test_cluster_run_kdk_matches_oracle(nbm, n):
+    s = ics.cube(n, seed=900 + n)
+    ctx = _ctx(nbm, CLUSTER, G=0.8, eps=0.02, dt=2e-3, scheme="kdk")
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    ctx.run(x, v, m, 12)
+    ctx.sync()
+    xr, vr = oracle.run(s.x, s.v, s.m, 0.8, 0.02, 2e-3, 12, scheme="kdk")
+    assert rel_l2(to_np(x), xr) <= 1e-5
+    assert rel_l2(to_np(v), vr) <= 1e-4
+
+
+def test_cluster_and_graph_paths_agree_with_checkpoints(nbm):
+    n, steps, k = 777, 12, 4
+    s = ics.cube(n, seed=31)
+    out = {}
+    for path in (GRAPH, CLUSTER):
+        ctx = _ctx(nbm, path)
+        x, v, m = _t(s.x), _t(s.v), _t(s.m)
+        ck = torch.zeros((steps // k + 1, n, 6), dtype=torch.float32, device=DEV)
+        ctx.run(x, v, m, steps, ckpt=ck, ckpt_every=k)
+        ctx.sync()
+        out[path] = (to_np(x), to_np(v), to_np(ck))
+    xg, vg, cg = out[GRAPH]
+    xc, vc, cc = out[CLUSTER]
+    assert np.array_equal(cc[0][:, :3], s.x.astype(np.float32))  # slot 0 is the input state
+    assert np.array_equal(cc[0][:, 3:], s.v.astype(np.float32))
+    assert rel_l2(xc, xg) <= 1e-6 and rel_l2(vc, vg) <= 1e-5
+    for slot in range(1, steps // k + 1):
+        assert rel_l2(cc[slot], cg[slot]) <= 1e-5
+    assert np.array_equal(cc[-1][:, :3], xc) and np.array_equal(cc[-1][:, 3:], vc)
+
+
+def test_default_path_choice(nbm):
+    """Untuned, the cluster path serves n <= 512 (one launch for all steps)
+    and the graph path larger systems (one force launch per step)."""
+    for n, launches in ((512, 1), (1024, 11)):
+        s = ics.cube(n, seed=3)
+        ctx = nbm.Context(1.0, 0.01, 1e-3)
+        x, v, m = _t(s.x), _t(s.v), _t(s.m)
+        ctx.run(x, v, m, 10)
+        ctx.sync()
+        before = ctx.launch_count
+        ctx.run(x, v, m, 10)
+        ctx.sync()
+        assert ctx.launch_count - before == launches, n
+
+
+def test_autotune_keeps_run_correct(nbm):
+    n = 1024
+    s = ics.cube(n, seed=0)
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    ctx.autotune(n)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    ctx.run(x, v, m, 10)
+    ctx.sync()
+    xr, _ = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 10)
+    assert rel_l2(to_np(x), xr) <= 1e-5
+
+
+def test_cluster_path_refuses_what_it_cannot_run(nbm):
+    s = ics.cube(5000, seed=1)
+    ctx = _ctx(nbm, CLUSTER)
+    with pytest.raises(RuntimeError):
+        ctx.run(_t(s.x), _t(s.v), _t(s.m), 2)  # above 4096 bodies
+    s = ics.cube(100, seed=1)
+    ctx = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, CLUSTER)
+    with pytest.raises(RuntimeError):
+        ctx.run(_t(s.x, torch.float64), _t(s.v, torch.float64), _t(s.m, torch.float64), 2)
