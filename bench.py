@@ -176,7 +176,8 @@ def run_reference(args):
 # GPU type. Most of it is split partials evicted from L2; the O(N) state is
 # 21 MB. Reported only when the bench runs one of these shapes.
 STEP_TRAFFIC_BYTES = {
-    (128, 8, 19, 64): 11.33e6 + 33.93e6,
+    (128, 8, 19, 128): 11.85e6 + 34.15e6,
+    (128, 8, 19, 64): 11.07e6 + 34.31e6,
     (128, 4, 16, 256): 11.16e6 + 21.29e6,
     (128, 8, 19, 256): 11.77e6 + 34.34e6,
     (128, 8, 26, 256): 12.73e6 + 63.50e6,
