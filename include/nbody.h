@@ -120,10 +120,11 @@ nb_status nb_step(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, void 
  * `steps` steps in place on x, v (Section 3.1's loop over the update), by one
  * of two paths with the same arithmetic: a CUDA graph of one force launch per
  * step that the context captures once per (n, buffers, steps, checkpoint
- * layout) and caches; or, for FP32 systems of at most 4096 bodies, one
- * kernel on one thread-block cluster that keeps the positions in distributed
- * shared memory across all steps. nb_autotune picks the faster path per size;
- * untuned, the cluster path serves n <= 512. ckpt (nullable, device):
+ * layout) and caches; or, for systems of at most 4096 bodies, one kernel on
+ * one thread-block cluster that keeps the positions in distributed shared
+ * memory across all steps. nb_autotune picks the faster path per size;
+ * untuned, the cluster path serves n <= 512 (FP32) or n <= 1024 (precision
+ * form). ckpt (nullable, device):
  * [steps/ckpt_every + 1][n][6] in the state type; slot k receives (x, v)
  * after k*ckpt_every steps (slot 0 = the input state). ckpt_every must divide
  * steps when ckpt != NULL. The paper scheme only when checkpointing.
@@ -213,7 +214,7 @@ nb_status nb_energy(nb_ctx *ctx, int64_t n, const void *x, const void *v, const 
  * Time the candidate kernel shapes for problems of size n in mode `mode`
  * (0 = forward, 1 = adjoint VJP) and store the fastest in the context's
  * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). In
- * mode 0 with FP32 state and n <= 4096 it also times nb_run's two paths
+ * mode 0 with n <= 4096 it also times nb_run's two paths
  * (graph of force launches, one-cluster kernel) and records the faster. Calls
  * that find no entry for their size bucket use a built-in heuristic instead.
  * Synchronous.

@@ -95,16 +95,17 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     NB_TRY(sync_and_check(ctx, st));
     ctx->tuned[tune_key(ctx, mode, n)] = best;
     clear_graphs(ctx);
-    // nb_run's two paths for small FP32 systems: the graph of force launches
+    // nb_run's two paths for small systems: the graph of force launches
     // (with the shape just chosen) against the one-cluster kernel, 20 steps
     // each on zeroed state (timing does not depend on the values)
     int cluster = 0;
-    if (mode == 0 && !f64_state(ctx) && ctx->math == 0 && n <= kClusterMaxN) cluster = cluster_run_size(n);
+    const bool f64 = f64_state(ctx);
+    if (mode == 0 && (f64 || ctx->math == 0) && n <= kClusterMaxN) cluster = cluster_run_size(n, f64);
     if (cluster) {
-        float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[4].p, *m = (float *)ctx->tune[3].p;
-        NB_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 12, st));
-        NB_CUDA(cudaMemsetAsync(v, 0, (size_t)n * 12, st));
-        NB_CUDA(cudaMemsetAsync(m, 0, (size_t)n * 4, st));
+        void *x = ctx->tune[1].p, *v = ctx->tune[4].p, *m = ctx->tune[3].p;
+        NB_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 3 * esize(ctx), st));
+        NB_CUDA(cudaMemsetAsync(v, 0, (size_t)n * 3 * esize(ctx), st));
+        NB_CUDA(cudaMemsetAsync(m, 0, (size_t)n * esize(ctx), st));
         const int steps = 20;
         const int saved_path = ctx->run_path;
         float ms_path[2] = {1e30f, 1e30f};

@@ -14,6 +14,7 @@
 // launch, bulk-copy and split-reduction latencies dominate, and this path
 // removes them.
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.h"
 #include "engine.cuh"
@@ -25,10 +26,11 @@ namespace {
 struct ClusterArgs {
     int n, npad, slice;  // bodies, cluster size x slice, bodies per CTA (even)
     int steps, kdk;      // paper steps; 1: kick-drift-kick scheme
-    float eps2, G, dt;
-    float *x, *v;        // [n][3], updated in place
-    const float *m;      // [n]
-    float *ckpt;         // nullable: slots of [n][6] (x, v), slot s after step s * ckpt_every
+    float eps2;
+    double G, dt;
+    void *x, *v;         // [n][3] in the state type, updated in place
+    const void *m;       // [n] in the state type
+    void *ckpt;          // nullable: slots of [n][6] (x, v), slot s after step s * ckpt_every
     int ckpt_every;
 };
 
@@ -76,9 +78,23 @@ __device__ __forceinline__ int lanes_per_body(int slice) {
     return q;
 }
 
-template <int NT>
+// Pair-sum block of the precision form: FP32 packed partial sums over this
+// many j-pairs of a lane, then a two-sum into the lane's (hi, lo) total, as
+// the graph path does per 64-body tile.
+constexpr int kCompBlockPairs = 32;
+constexpr int kClusterMaxSlice = 512;  // bodies per CTA (the launch keeps slice <= threads)
+
+// F64 = false: FP32 state and forces (AccelF32x2). F64 = true: the precision
+// form, FP64 state, FP32 pair terms summed in blocks, two-sums across blocks,
+// FP64 across lanes and in the update (AccelComp's arithmetic).
+template <int NT, bool F64>
 __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a) {
+    using TS = typename std::conditional<F64, double, float>::type;
     extern __shared__ __align__(16) float4 rep[];  // [2][npad] packed pair records
+    const TS *xg = reinterpret_cast<const TS *>(a.x);
+    const TS *vg = reinterpret_cast<const TS *>(a.v);
+    const TS *mg = reinterpret_cast<const TS *>(a.m);
+    TS *ckpt = reinterpret_cast<TS *>(a.ckpt);
     const int tid = threadIdx.x;
     const uint32_t rank = cluster_ctarank();
     const uint32_t csize = cluster_nctarank();
@@ -86,28 +102,35 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
     const int npad = a.npad;
     const int Q = lanes_per_body<NT>(S);
     const int il = tid / Q, jq = tid % Q;
-    const bool active = il < S;                    // sums forces for body i
+    const bool active = il < S;  // sums forces for body i
     const int i = (int)rank * S + (active ? il : 0);
-    const bool owner = active && jq == 0 && i < a.n;  // updates body i
+    // The thread that keeps body io's x and v and updates it: the first lane
+    // of the body's group in FP32; in the precision form thread k of the CTA
+    // for body k of the slice, so that the FP64 update (slow on this part)
+    // fills ceil(S / 32) warps instead of one warp per body.
+    const int io = (int)rank * S + (F64 ? tid : il);
+    const bool owner = F64 ? (tid < S && io < a.n) : (active && jq == 0 && i < a.n);
+    __shared__ float s_hl[F64 ? kClusterMaxSlice : 1][6];  // precision form: a body's (hi, lo) sums
 
     // both replicas: every body's record in buffer 0, zeros in buffer 1
     for (int k = tid; k < npad; k += NT) {
         if (k < a.n)
-            pair_put(rep, k, a.x[3 * k], a.x[3 * k + 1], a.x[3 * k + 2], a.m[k]);
+            pair_put(rep, k, (float)xg[3 * k], (float)xg[3 * k + 1], (float)xg[3 * k + 2], (float)mg[k]);
         else
             pair_put(rep, k, 0.f, 0.f, 0.f, 0.f);
         pair_put(rep + npad, k, 0.f, 0.f, 0.f, 0.f);
     }
-    float xs[3] = {0.f, 0.f, 0.f}, vs[3] = {0.f, 0.f, 0.f}, mi = 0.f;
+    TS xs[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
+    float mi = 0.f;
     if (owner) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            xs[c] = a.x[3 * i + c];
-            vs[c] = a.v[3 * i + c];
+            xs[c] = xg[3 * io + c];
+            vs[c] = vg[3 * io + c];
         }
-        mi = a.m[i];
-        if (a.ckpt) {
-            float *ck = a.ckpt + 6 * (int64_t)i;
+        mi = (float)mg[io];
+        if (ckpt) {
+            TS *ck = ckpt + 6 * (int64_t)io;
             ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
             ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
         }
@@ -115,53 +138,115 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
     // no CTA writes into another's buffer 1 before that one has zeroed it
     cluster_barrier();
 
-    const float dt = a.dt;
     const int evals = a.steps + (a.kdk && a.steps > 0 ? 1 : 0);
     int cur = 0;
     for (int t = 0; t < evals; ++t) {
         const float4 *src = rep + cur * npad;
         float4 *dst = rep + (cur ^ 1) * npad;
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        if (active) {
-            AccelF32x2::I ist;
+        TS ax = 0, ay = 0, az = 0;
+        AccelF32x2::I ist;
+        AccelF32x2::C cst;
+        cst.eps2 = dup(a.eps2);
+        ist.nx = dup(-pair_get(src, i, 0));
+        ist.ny = dup(-pair_get(src, i, 1));
+        ist.nz = dup(-pair_get(src, i, 2));
+        const int npairs = npad >> 1;
+        if constexpr (!F64) {
             AccelF32x2::T tot;
-            AccelF32x2::C cst;
-            cst.eps2 = dup(a.eps2);
-            ist.nx = dup(-pair_get(src, i, 0));
-            ist.ny = dup(-pair_get(src, i, 1));
-            ist.nz = dup(-pair_get(src, i, 2));
             AccelF32x2::zero_total(tot);
-            const int npairs = npad >> 1;
+            if (active) {
 #pragma unroll 4
-            for (int p = jq; p < npairs; p += Q) {
-                const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
-                AccelF32x2::interact(rec, ist, tot, cst);
+                for (int p = jq; p < npairs; p += Q) {
+                    const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
+                    AccelF32x2::interact(rec, ist, tot, cst);
+                }
             }
             ax = tot.x.x + tot.x.y;
             ay = tot.y.x + tot.y.y;
             az = tot.z.x + tot.z.y;
-        }
-        for (int off = Q >> 1; off > 0; off >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, off);
-            ay += __shfl_xor_sync(0xffffffffu, ay, off);
-            az += __shfl_xor_sync(0xffffffffu, az, off);
+            for (int off = Q >> 1; off > 0; off >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, off);
+                ay += __shfl_xor_sync(0xffffffffu, ay, off);
+                az += __shfl_xor_sync(0xffffffffu, az, off);
+            }
+        } else {
+            // per-lane (hi, lo) totals over blocks of FP32 partial sums ...
+            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+            if (active) {
+                for (int p0 = jq; p0 < npairs; p0 += Q * kCompBlockPairs) {
+                    AccelF32x2::T blk;
+                    AccelF32x2::zero_total(blk);
+                    const int pend = min(npairs, p0 + Q * kCompBlockPairs);
+#pragma unroll 4
+                    for (int p = p0; p < pend; p += Q) {
+                        const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
+                        AccelF32x2::interact(rec, ist, blk, cst);
+                    }
+                    const float b3[3] = {blk.x.x + blk.x.y, blk.y.x + blk.y.y, blk.z.x + blk.z.y};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float sum, err;
+                        two_sum(h[c], b3[c], sum, err);
+                        h[c] = sum;
+                        l[c] += err;
+                    }
+                }
+            }
+            // ... combined across the body's lanes with FP32 two-sums (the FP64
+            // pipe is slow on this part), and widened once, in the owner
+            for (int off = Q >> 1; off > 0; off >>= 1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h[c], off);
+                    const float ol = __shfl_xor_sync(0xffffffffu, l[c], off);
+                    float sum, err;
+                    two_sum(h[c], oh, sum, err);
+                    h[c] = sum;
+                    l[c] = __fadd_rn(__fadd_rn(l[c], ol), err);
+                }
+            }
+            if (active && jq == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    s_hl[il][c] = h[c];
+                    s_hl[il][3 + c] = l[c];
+                }
+            }
+            __syncthreads();
+            if (owner) {
+                ax = (double)s_hl[tid][0] + (double)s_hl[tid][3];
+                ay = (double)s_hl[tid][1] + (double)s_hl[tid][4];
+                az = (double)s_hl[tid][2] + (double)s_hl[tid][5];
+            }
         }
         const bool last_kick = a.kdk && t == a.steps;  // the closing half kick of KDK
         if (owner) {
-            const float acc[3] = {a.G * ax, a.G * ay, a.G * az};
             const bool double_kick = a.kdk && t > 0 && !last_kick;
+            if constexpr (!F64) {
+                const float G = (float)a.G, dt = (float)a.dt;
+                const float acc[3] = {G * ax, G * ay, G * az};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                // v <- v + a*dt/2 (twice between two drifts of the KDK scheme), then x += v*dt
-                float vc = __fadd_rn(vs[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
-                if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
-                vs[c] = vc;
-                if (!last_kick) xs[c] = __fadd_rn(xs[c], __fmul_rn(vc, dt));
+                for (int c = 0; c < 3; ++c) {
+                    // v <- v + a*dt/2 (twice between two drifts of the KDK scheme), then x += v*dt
+                    float vc = __fadd_rn(vs[c], __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
+                    if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[c], dt), 0.5f));
+                    vs[c] = vc;
+                    if (!last_kick) xs[c] = __fadd_rn(xs[c], __fmul_rn(vc, dt));
+                }
+            } else {
+                const double acc[3] = {a.G * ax, a.G * ay, a.G * az};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double vc = __dadd_rn(vs[c], __dmul_rn(__dmul_rn(acc[c], a.dt), 0.5));
+                    if (double_kick) vc = __dadd_rn(vc, __dmul_rn(__dmul_rn(acc[c], a.dt), 0.5));
+                    vs[c] = vc;
+                    if (!last_kick) xs[c] = __dadd_rn(xs[c], __dmul_rn(vc, a.dt));
+                }
             }
             if (!last_kick) {
-                pair_put(dst, i, xs[0], xs[1], xs[2], mi);
-                if (a.ckpt && (t + 1) % a.ckpt_every == 0) {
-                    float *ck = a.ckpt + (int64_t)((t + 1) / a.ckpt_every) * 6 * a.n + 6 * (int64_t)i;
+                pair_put(dst, io, (float)xs[0], (float)xs[1], (float)xs[2], mi);
+                if (ckpt && (t + 1) % a.ckpt_every == 0) {
+                    TS *ck = ckpt + (int64_t)((t + 1) / a.ckpt_every) * 6 * a.n + 6 * (int64_t)io;
                     ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
                     ck[3] = vs[0]; ck[4] = vs[1]; ck[5] = vs[2];
                 }
@@ -181,10 +266,12 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
         cur ^= 1;
     }
     if (owner) {
+        TS *xw = reinterpret_cast<TS *>(a.x);
+        TS *vw = reinterpret_cast<TS *>(a.v);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            a.x[3 * i + c] = xs[c];
-            a.v[3 * i + c] = vs[c];
+            xw[3 * io + c] = xs[c];
+            vw[3 * io + c] = vs[c];
         }
     }
 }
@@ -196,9 +283,15 @@ constexpr int kClusterThreads = 512;
 // Largest cluster this device can run the kernel with for n bodies (16 if
 // non-portable clusters are allowed and fit, else 8), 0 if none: the two
 // replicas must fit in shared memory.
-int cluster_run_size(int64_t n) {
+using ClusterFn = void (*)(const ClusterArgs);
+
+ClusterFn cluster_fn(bool f64) {
+    return f64 ? cluster_run_kernel<kClusterThreads, true> : cluster_run_kernel<kClusterThreads, false>;
+}
+
+int cluster_run_size(int64_t n, bool f64) {
     if (n <= 0 || n > kClusterMaxN) return 0;
-    auto fn = cluster_run_kernel<kClusterThreads>;
+    ClusterFn fn = cluster_fn(f64);
     for (int c : {16, 8}) {
         const int64_t slice = ((n + c - 1) / c + 1) / 2 * 2;
         if (slice > kClusterThreads) continue;
@@ -228,11 +321,11 @@ int cluster_run_size(int64_t n) {
     return 0;
 }
 
-cudaError_t launch_cluster_run(int cluster, int64_t n, float *x, float *v, const float *m, int steps,
-                               int kdk, float eps2, float G, float dt, float *ckpt, int ckpt_every,
-                               cudaStream_t st) {
+cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *v, const void *m,
+                               int steps, int kdk, float eps2, double G, double dt, void *ckpt,
+                               int ckpt_every, cudaStream_t st) {
     if (cluster <= 0 || n <= 0 || n > kClusterMaxN) return cudaErrorInvalidValue;
-    auto fn = cluster_run_kernel<kClusterThreads>;
+    ClusterFn fn = cluster_fn(f64);
     ClusterArgs a;
     a.n = (int)n;
     a.slice = (int)(((n + cluster - 1) / cluster + 1) / 2 * 2);

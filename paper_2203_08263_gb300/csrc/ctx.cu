@@ -321,11 +321,13 @@ nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
     *cluster = 0;
     if (ctx->run_path == 1) return NB_OK;
     int c = 0;
-    if (!f64_state(ctx) && ctx->math == 0 && n <= kClusterMaxN) {
-        auto it = ctx->cluster_sizes.find(n);
+    const bool f64 = f64_state(ctx);
+    if ((f64 || ctx->math == 0) && n <= kClusterMaxN) {
+        const int64_t key = 2 * n + (f64 ? 1 : 0);
+        auto it = ctx->cluster_sizes.find(key);
         if (it == ctx->cluster_sizes.end()) {
-            c = cluster_run_size(n);
-            ctx->cluster_sizes[n] = c;
+            c = cluster_run_size(n, f64);
+            ctx->cluster_sizes[key] = c;
         } else {
             c = it->second;
         }
@@ -333,8 +335,8 @@ nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
     if (ctx->run_path == 2) {
         if (!c)
             return fail(ctx, NB_ERR_UNSUPPORTED,
-                        "the one-cluster path runs FP32 systems of at most %lld bodies (MUFU "
-                        "denominator) that fit a cluster on this device",
+                        "the one-cluster path runs systems of at most %lld bodies (FP32 with the "
+                        "MUFU denominator, or the precision form) that fit a cluster on this device",
                         (long long)kClusterMaxN);
         *cluster = c;
         return NB_OK;
@@ -344,7 +346,7 @@ nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
     if (t != ctx->tuned.end())
         *cluster = t->second.pol ? c : 0;
     else
-        *cluster = n <= kClusterDefaultN ? c : 0;
+        *cluster = n <= (f64 ? kClusterDefaultN64 : kClusterDefaultN) ? c : 0;
     return NB_OK;
 }
 
@@ -353,10 +355,10 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
     int cluster = 0;
     NB_TRY(choose_run_path(ctx, n, &cluster));
     if (cluster) {
-        NB_CUDA(launch_cluster_run(cluster, n, (float *)x, (float *)v, (const float *)m, steps,
+        NB_CUDA(launch_cluster_run(cluster, n, f64_state(ctx), x, v, m, steps,
                                    ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0,
-                                   (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
-                                   (float)ctx->p.dt, (float *)ckpt, ckpt_every, st));
+                                   (float)(ctx->p.eps * ctx->p.eps), ctx->p.G, ctx->p.dt, ckpt,
+                                   ckpt_every, st));
         ctx->launches += 1;
         return NB_OK;
     }

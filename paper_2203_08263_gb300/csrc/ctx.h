@@ -53,7 +53,7 @@ struct nb_ctx {
     int debug = 0;
     int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
     int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one-cluster kernel
-    std::map<int64_t, int> cluster_sizes;  // n -> cluster size of the one-cluster path (0: none)
+    std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;
     std::map<uint64_t, nb::BatchPlan> batched_tuned;  // size profile -> tuned batched shape

@@ -69,18 +69,23 @@ cudaError_t measure_peaks(int blocks, float *sink, cudaStream_t st, double out[3
 
 // Small systems in one cluster launch (csrc/cluster.cu): every step of a run
 // in one kernel, positions replicated in the shared memory of each CTA of one
-// thread-block cluster and exchanged through distributed shared memory.
+// thread-block cluster and exchanged through distributed shared memory; FP32
+// or the precision form.
 constexpr int64_t kClusterMaxN = 4096;      // two replicas of 64 KiB
-// Untuned, the cluster path serves systems up to this size: measured on
-// GB300 at 100 steps, 1.9 vs 5.2 us per step at N = 256 and 3.5 vs 5.7 at
-// N = 512, but 9.7 vs 7.4 at N = 1024, where the graph path's 152 SMs outrun
-// one cluster's 16.
+// Untuned, the cluster path serves systems up to these sizes. Measured on
+// GB300 at 100 steps, us per step cluster vs graph: FP32 1.9 vs 5.2 at
+// N = 256, 3.5 vs 5.7 at 512, 9.6 vs 5.9 at 1024 (the graph path's 152 SMs
+// outrun one cluster's 16); precision form 3.3 vs 11.3 at 256, 10.8 vs 18.0
+// at 1024, 21.2 vs 22.0 at 2048, 67.8 vs 29.9 at 4096 (its graph path pays
+// FP64 epilogues per step).
 constexpr int64_t kClusterDefaultN = 512;
+constexpr int64_t kClusterDefaultN64 = 1024;
 // Cluster size (16, or 8 where 16 cannot be scheduled) for n bodies; 0 if
 // the path cannot run n bodies on this device.
-int cluster_run_size(int64_t n);
-cudaError_t launch_cluster_run(int cluster, int64_t n, float *x, float *v, const float *m, int steps,
-                               int kdk, float eps2, float G, float dt, float *ckpt, int ckpt_every,
-                               cudaStream_t st);
+// f64: the precision form (FP64 state, compensated FP32 forces).
+int cluster_run_size(int64_t n, bool f64);
+cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *v, const void *m,
+                               int steps, int kdk, float eps2, double G, double dt, void *ckpt,
+                               int ckpt_every, cudaStream_t st);
 
 }  // namespace nb

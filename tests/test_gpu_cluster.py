@@ -113,7 +113,69 @@ def test_cluster_path_refuses_what_it_cannot_run(nbm):
     with pytest.raises(RuntimeError):
         ctx.run(_t(s.x), _t(s.v), _t(s.m), 2)  # above 4096 bodies
     s = ics.cube(100, seed=1)
-    ctx = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
-    ctx.debug_set(nbm.NB_DBG_RUN_PATH, CLUSTER)
+    ctx = _ctx(nbm, CLUSTER)
+    ctx.debug_set(nbm.NB_DBG_MATH_VARIANT, 1)  # the sqrt-then-divide ablation has no cluster form
     with pytest.raises(RuntimeError):
-        ctx.run(_t(s.x, torch.float64), _t(s.v, torch.float64), _t(s.m, torch.float64), 2)
+        ctx.run(_t(s.x), _t(s.v), _t(s.m), 2)
+
+
+# ---------------------------------------------------------- precision form
+
+def _ctx64(nbm, path, G=1.0, eps=0.05, dt=5e-4, scheme="paper"):
+    ctx = nbm.Context(G, eps, dt, precision="comp", scheme=scheme)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, path)
+    return ctx
+
+
+def _t64(a):
+    return _t(a, torch.float64)
+
+
+@pytest.mark.parametrize("n", [3, 300, 2048, 4096])
+def test_cluster_precision_form_matches_oracle(nbm, n):
+    """FP64 state, compensated FP32 forces: the tolerances of the graph
+    path's precision-form run test (C3 setting, Plummer)."""
+    s = ics.plummer(n, seed=2)
+    ctx = _ctx64(nbm, CLUSTER)
+    x, v, m = _t64(s.x), _t64(s.v), _t64(s.m)
+    ctx.run(x, v, m, 10)
+    ctx.sync()
+    xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.05, 5e-4, 10)
+    assert rel_l2(to_np(x), xr) <= 1e-9
+    assert rel_l2(to_np(v), vr) <= 1e-6
+
+
+def test_default_path_choice_precision_form(nbm):
+    """Untuned, the precision form takes the cluster path up to n = 1024."""
+    for n, launches in ((1024, 1), (2048, 11)):
+        s = ics.plummer(n, seed=5)
+        ctx = nbm.Context(1.0, 0.05, 5e-4, precision="comp")
+        x, v, m = _t64(s.x), _t64(s.v), _t64(s.m)
+        ctx.run(x, v, m, 10)
+        ctx.sync()
+        before = ctx.launch_count
+        ctx.run(x, v, m, 10)
+        ctx.sync()
+        assert ctx.launch_count - before == launches, n
+
+
+def test_cluster_precision_form_kdk_and_checkpoints(nbm):
+    n = 1000
+    s = ics.plummer(n, seed=12)
+    ctx = _ctx64(nbm, CLUSTER, scheme="kdk")
+    x, v, m = _t64(s.x), _t64(s.v), _t64(s.m)
+    ctx.run(x, v, m, 8)
+    ctx.sync()
+    xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.05, 5e-4, 8, scheme="kdk")
+    assert rel_l2(to_np(x), xr) <= 1e-9 and rel_l2(to_np(v), vr) <= 1e-6
+    out = {}
+    for path in (GRAPH, CLUSTER):
+        ctx = _ctx64(nbm, path)
+        x, v, m = _t64(s.x), _t64(s.v), _t64(s.m)
+        ck = torch.zeros((3, n, 6), dtype=torch.float64, device=DEV)
+        ctx.run(x, v, m, 8, ckpt=ck, ckpt_every=4)
+        ctx.sync()
+        out[path] = to_np(ck)
+    assert np.array_equal(out[CLUSTER][0], out[GRAPH][0])  # the input state, exactly
+    for slot in (1, 2):
+        assert rel_l2(out[CLUSTER][slot], out[GRAPH][slot]) <= 1e-9
