@@ -383,6 +383,7 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
         const size_t slot_bytes = (size_t)n * 6 * esize(ctx);
         for (int t = 0; rs == NB_OK && t < steps; ++t) {
             ForceArgs a = base_args(ctx, p, n, xm[t & 1]);
+            a.pdl = 1;
             a.op = (kdk && t > 0) ? kEpiKick2Drift : kEpiKickDrift;
             a.x = x;
             a.v = v;
@@ -393,6 +394,7 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
         }
         if (rs == NB_OK && kdk && steps > 0) {
             ForceArgs a = base_args(ctx, p, n, xm[steps & 1]);
+            a.pdl = 1;
             a.op = kEpiKick;
             a.x = x;
             a.v = v;

@@ -100,6 +100,7 @@ struct ForceArgs {
     const void *abar64;   // [n][3] FP64 cotangent of a (precision form)
     const void *mass;     // [n] state-type masses (adjoint epilogue)
     int debug;            // bit 0: the producer issues no copies (timeout tests)
+    int pdl;              // host: launched as a programmatic dependent of the previous kernel
 };
 
 // ---------------------------------------------------------------- helpers
@@ -199,6 +200,12 @@ __global__ void __launch_bounds__(NT + kProducerThreads, (min_blocks<NT, R>())) 
         }
         mbar_init_fence();
     }
+    // Launched as a programmatic dependent (a step of nb_run after the
+    // previous one), this grid may be scheduled while the previous kernel
+    // finishes: wait until that grid has completed and its writes
+    // (positions, partials, counters) are visible before touching global
+    // memory. A no-op in an ordinary launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
 
     typename P::T tot[R];
@@ -373,6 +380,12 @@ __global__ void __launch_bounds__(NT + kProducerThreads, (min_blocks<NT, R>())) 
 #endif
 
     // ---------------- epilogue (all threads reach the barriers below)
+    // The pair sums are done: once every CTA of this grid is here (or has
+    // exited), the next step's grid may be scheduled and wait in its
+    // prologue. Triggering at entry instead let the next grid's CTAs take
+    // the first free SM slots and pile onto few SMs: 1.5-2x slower steps at
+    // N = 3072-4096 (measured).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const bool consumer = warp < NT / 32;
     if (args.split == 1) {
         if (consumer) {

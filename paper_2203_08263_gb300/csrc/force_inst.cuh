@@ -1,6 +1,8 @@
 // Instantiation helpers: one translation unit per policy keeps the build
 // parallel. Each entry pairs a launcher with an occupancy query.
 #pragma once
+#include <cstring>
+
 #include "kernels.h"
 
 namespace nb {
@@ -14,8 +16,24 @@ cudaError_t launch_force_inst(int jt, const ForceArgs &a, cudaStream_t st) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)((int64_t)a.iblocks * a.split), NT + kProducerThreads, smem, st>>>(a);
-    return cudaGetLastError();
+    if (!a.pdl) {
+        k<<<(unsigned)((int64_t)a.iblocks * a.split), NT + kProducerThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    // programmatic dependent launch: the grid may be scheduled before the
+    // previous kernel on the stream completes; the kernel waits for it
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)((int64_t)a.iblocks * a.split));
+    cfg.blockDim = dim3(NT + kProducerThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 template <class P, int NT, int R>
