@@ -681,8 +681,9 @@ struct AccelMath {
 // Precision form: FP32 pair terms (optionally one Newton-Raphson refinement
 // of the MUFU reciprocal square root, y <- y (3/2 - s y^2 / 2), see
 // NB_COMP_NEWTON), plain FP32 sums within a j-tile, and the per-tile sums
-// folded into a (hi, lo) pair with Knuth's two-sum. Split partials carry (hi, lo); the final reduction and the
-// update run in FP64.
+// folded into a (hi, lo) pair with Knuth's two-sum. Split partials carry
+// (hi, lo) and are folded the same way in split order; the sum is widened to
+// FP64 once, and the update runs in FP64.
 struct AccelComp {
     static constexpr int UNROLL = NB_UNROLL_OR(1);
     static constexpr bool SELF_MASK = false;
@@ -692,7 +693,7 @@ struct AccelComp {
     using I = AccelF32x2::I;
     struct A { float2 x, y, z; };
     struct T { float hx, hy, hz, lx, ly, lz; };
-    struct F { double x, y, z; };
+    using F = T;  // across splits: the same (hi, lo) two-sums, widened to FP64 once
     struct C { float2 eps2, mhalf, three_half; };
     __device__ static void consts(const ForceArgs &a, C &c) {
         c.eps2 = dup(a.eps2);
@@ -733,20 +734,21 @@ struct AccelComp {
         dst[0] = make_float4(t.hx, t.hy, t.hz, 0.f);
         dst[1] = make_float4(t.lx, t.ly, t.lz, 0.f);
     }
-    __device__ static void zero_final(F &f) { f.x = f.y = f.z = 0.0; }
+    __device__ static void zero_final(F &f) { zero_total(f); }
+    // One split's (hi, lo) partial into the running (hi, lo): the FP32
+    // two-sum keeps about 2^-44 relative, and the FP64 pipe (slow on this
+    // part) is left to the update.
     __device__ static void add_part(F &f, const float4 *src) {
-        float4 h = __ldcg(src), l = __ldcg(src + 1);
-        f.x += (double)h.x + (double)l.x;
-        f.y += (double)h.y + (double)l.y;
-        f.z += (double)h.z + (double)l.z;
+        const float4 h = __ldcg(src), l = __ldcg(src + 1);
+        float s, e;
+        two_sum(f.hx, h.x, s, e); f.hx = s; f.lx = __fadd_rn(f.lx, __fadd_rn(l.x, e));
+        two_sum(f.hy, h.y, s, e); f.hy = s; f.ly = __fadd_rn(f.ly, __fadd_rn(l.y, e));
+        two_sum(f.hz, h.z, s, e); f.hz = s; f.lz = __fadd_rn(f.lz, __fadd_rn(l.z, e));
     }
-    __device__ static void from_total(F &f, const T &t) {
-        f.x = (double)t.hx + (double)t.lx;
-        f.y = (double)t.hy + (double)t.ly;
-        f.z = (double)t.hz + (double)t.lz;
-    }
+    __device__ static void from_total(F &f, const T &t) { f = t; }
     __device__ static void finish(const ForceArgs &a, int64_t i, const F &f) {
-        finish_fp64(a, i, a.G * f.x, a.G * f.y, a.G * f.z);
+        finish_fp64(a, i, a.G * ((double)f.hx + (double)f.lx), a.G * ((double)f.hy + (double)f.ly),
+                    a.G * ((double)f.hz + (double)f.lz));
     }
 };
 
@@ -915,8 +917,8 @@ struct VjpF32x2 {
 // FP64 state, and d = (x_j^hi - x_k^hi) + (x_j^lo - x_k^lo) keeps its
 // relative error at FP32 rounding even for close pairs (whose terms weigh
 // as |d|^-3); the rsqrt is refined only with NB_COMP_NEWTON; sums are FP32 within a tile
-// and two-summed (hi, lo) across tiles; the epilogue runs in FP64 with FP64
-// m_k and abar_k. Records, 5 float4 per pair of bodies:
+// and two-summed (hi, lo) across tiles and splits; the epilogue widens them
+// and runs in FP64 with FP64 m_k and abar_k. Records, 5 float4 per pair of bodies:
 //   {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,xl0,xl1} {yl0,yl1,zl0,zl1}
 struct VjpComp {
     static constexpr int UNROLL = NB_UNROLL_OR(2);
@@ -930,7 +932,7 @@ struct VjpComp {
     };
     using A = VjpF32x2::T;
     struct T { float h[8], l[8]; };
-    struct F { double s[8]; };
+    using F = T;  // across splits: the same (hi, lo) two-sums, widened to FP64 in finish
     struct C { float2 eps2, mhalf, three_half; };
     __device__ static void consts(const ForceArgs &a, C &c) {
         c.eps2 = dup(a.eps2);
@@ -1004,30 +1006,34 @@ struct VjpComp {
         dst[2] = make_float4(t.l[0], t.l[1], t.l[2], t.l[3]);
         dst[3] = make_float4(t.l[4], t.l[5], t.l[6], t.l[7]);
     }
-    __device__ static void zero_final(F &f) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f.s[k] = 0.0;
-    }
+    __device__ static void zero_final(F &f) { zero_total(f); }
+    // One split's (hi, lo) partials into the running (hi, lo) with FP32
+    // two-sums (about 2^-44 relative), in split order.
     __device__ static void add_part(F &f, const float4 *src) {
         const float4 h0 = __ldcg(src), h1 = __ldcg(src + 1), l0 = __ldcg(src + 2),
                      l1 = __ldcg(src + 3);
         const float hh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
         const float ll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) f.s[k] += (double)hh[k] + (double)ll[k];
+        for (int k = 0; k < 8; ++k) {
+            float s, e;
+            two_sum(f.h[k], hh[k], s, e);
+            f.h[k] = s;
+            f.l[k] = __fadd_rn(f.l[k], __fadd_rn(ll[k], e));
+        }
     }
-    __device__ static void from_total(F &f, const T &t) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f.s[k] = (double)t.h[k] + (double)t.l[k];
-    }
+    __device__ static void from_total(F &f, const T &t) { f = t; }
     __device__ static void finish(const ForceArgs &a, int64_t k, const F &f) {
+        double fs[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) fs[q] = (double)f.h[q] + (double)f.l[q];
         const double G = a.G;
         const double mk = reinterpret_cast<const double *>(a.mass)[k];
         const double *ak = reinterpret_cast<const double *>(a.abar64) + 3 * k;
         double *xb = reinterpret_cast<double *>(a.xbar) + 3 * k;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * f.s[c] - f.s[3] * ak[c] + 3.0 * f.s[4 + c]);
-        reinterpret_cast<double *>(a.mbar)[k] += -G * f.s[7];
+        for (int c = 0; c < 3; ++c) xb[c] += G * (mk * fs[c] - fs[3] * ak[c] + 3.0 * fs[4 + c]);
+        reinterpret_cast<double *>(a.mbar)[k] += -G * fs[7];
     }
 };
 

@@ -75,9 +75,9 @@ constexpr int64_t kClusterMaxN = 4096;      // two replicas of 64 KiB
 // Untuned, the cluster path serves systems up to these sizes. Measured on
 // GB300 at 100 steps, us per step cluster vs graph: FP32 1.9 vs 5.2 at
 // N = 256, 3.5 vs 5.7 at 512, 9.6 vs 5.9 at 1024 (the graph path's 152 SMs
-// outrun one cluster's 16); precision form 3.3 vs 11.3 at 256, 10.8 vs 18.0
-// at 1024, 21.2 vs 22.0 at 2048, 67.8 vs 29.9 at 4096 (its graph path pays
-// FP64 epilogues per step).
+// outrun one cluster's 16); precision form 3.3 vs 8.5 at 256, 10.8 vs 10.9
+// at 1024, 21.2 vs 13.2 at 2048 (its graph path's FP64 update per step
+// costs more at small N).
 constexpr int64_t kClusterDefaultN = 512;
 constexpr int64_t kClusterDefaultN64 = 1024;
 // Cluster size (16, or 8 where 16 cannot be scheduled) for n bodies; 0 if
