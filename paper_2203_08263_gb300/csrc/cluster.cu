@@ -68,21 +68,10 @@ __device__ __forceinline__ void cluster_barrier() {
                      : "memory");
 }
 
-// Threads per body in the force sum: the largest power of two Q <= 32 with
-// slice x Q <= NT (the Q lanes of a body split its j-pairs and are reduced
-// with shuffles).
-template <int NT>
-__device__ __forceinline__ int lanes_per_body(int slice) {
-    int q = 1;
-    while (q < 32 && slice * q * 2 <= NT) q *= 2;
-    return q;
-}
-
 // Pair-sum block of the precision form: FP32 packed partial sums over this
 // many j-pairs of a lane, then a two-sum into the lane's (hi, lo) total, as
 // the graph path does per 64-body tile.
 constexpr int kCompBlockPairs = 32;
-constexpr int kClusterMaxSlice = 512;  // bodies per CTA (the launch keeps slice <= threads)
 
 // F64 = false: FP32 state and forces (AccelF32x2). F64 = true: the precision
 // form, FP64 state, FP32 pair terms summed in blocks, two-sums across blocks,
@@ -100,18 +89,24 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
     const uint32_t csize = cluster_nctarank();
     const int S = a.slice;
     const int npad = a.npad;
-    const int Q = lanes_per_body<NT>(S);
-    const int il = tid / Q, jq = tid % Q;
-    const bool active = il < S;  // sums forces for body i
+    // Thread mapping of the force sum: lane l of warp w sums body
+    // il = (w / Q) * 32 + l over the j-pairs jq, jq + Q, ... with jq = w % Q,
+    // so all lanes of a warp read the same j-record (a broadcast load: the
+    // j-split across lanes of one warp cost 8 shared-memory wavefronts per
+    // 16-byte load). The Q partial sums of a body meet in shared memory.
+    const int spad = (S + 31) / 32 * 32;  // body slots in whole warps
+    const int Q = NT / spad;              // j-splits per body (>= 1: slice <= NT)
+    const int warp = tid >> 5, lane = tid & 31;
+    const int jq = warp % Q;
+    const int il = (warp / Q) * 32 + lane;
+    const bool active = warp < Q * (spad / 32) && il < S;  // sums forces for body i
     const int i = (int)rank * S + (active ? il : 0);
-    // The thread that keeps body io's x and v and updates it: the first lane
-    // of the body's group in FP32; in the precision form thread k of the CTA
-    // for body k of the slice, so that the FP64 update (slow on this part)
-    // fills ceil(S / 32) warps instead of one warp per body.
-    const int io = (int)rank * S + (F64 ? tid : il);
-    const bool owner = F64 ? (tid < S && io < a.n) : (active && jq == 0 && i < a.n);
-    __shared__ float s_hl[F64 ? kClusterMaxSlice : 1][6];  // precision form: a body's (hi, lo) sums
-
+    // The thread that keeps body io's x and v and updates it: thread k of the
+    // CTA for body k of the slice (the update's FP64 in the precision form is
+    // slow on this part; compact owners fill ceil(S / 32) warps).
+    const int io = (int)rank * S + tid;
+    const bool owner = tid < S && io < a.n;
+    __shared__ float s_red[NT * (F64 ? 6 : 3)];  // per (split, body): partial sums (hi, lo)
     // both replicas: every body's record in buffer 0, zeros in buffer 1
     for (int k = tid; k < npad; k += NT) {
         if (k < a.n)
@@ -152,27 +147,32 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
         ist.nz = dup(-pair_get(src, i, 2));
         const int npairs = npad >> 1;
         if constexpr (!F64) {
-            AccelF32x2::T tot;
-            AccelF32x2::zero_total(tot);
             if (active) {
+                AccelF32x2::T tot;
+                AccelF32x2::zero_total(tot);
 #pragma unroll 4
                 for (int p = jq; p < npairs; p += Q) {
                     const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
                     AccelF32x2::interact(rec, ist, tot, cst);
                 }
+                float *r = s_red + 3 * (jq * spad + il);
+                r[0] = tot.x.x + tot.x.y;
+                r[1] = tot.y.x + tot.y.y;
+                r[2] = tot.z.x + tot.z.y;
             }
-            ax = tot.x.x + tot.x.y;
-            ay = tot.y.x + tot.y.y;
-            az = tot.z.x + tot.z.y;
-            for (int off = Q >> 1; off > 0; off >>= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, off);
-                ay += __shfl_xor_sync(0xffffffffu, ay, off);
-                az += __shfl_xor_sync(0xffffffffu, az, off);
+            __syncthreads();
+            if (owner) {
+                for (int q = 0; q < Q; ++q) {  // the body's splits in order
+                    const float *r = s_red + 3 * (q * spad + tid);
+                    ax += r[0];
+                    ay += r[1];
+                    az += r[2];
+                }
             }
         } else {
-            // per-lane (hi, lo) totals over blocks of FP32 partial sums ...
-            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+            // blocks of FP32 partial sums two-summed into (hi, lo) per split ...
             if (active) {
+                float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
                 for (int p0 = jq; p0 < npairs; p0 += Q * kCompBlockPairs) {
                     AccelF32x2::T blk;
                     AccelF32x2::zero_total(blk);
@@ -191,32 +191,30 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
                         l[c] += err;
                     }
                 }
-            }
-            // ... combined across the body's lanes with FP32 two-sums (the FP64
-            // pipe is slow on this part), and widened once, in the owner
-            for (int off = Q >> 1; off > 0; off >>= 1) {
+                float *r = s_red + 6 * (jq * spad + il);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, h[c], off);
-                    const float ol = __shfl_xor_sync(0xffffffffu, l[c], off);
-                    float sum, err;
-                    two_sum(h[c], oh, sum, err);
-                    h[c] = sum;
-                    l[c] = __fadd_rn(__fadd_rn(l[c], ol), err);
-                }
-            }
-            if (active && jq == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    s_hl[il][c] = h[c];
-                    s_hl[il][3 + c] = l[c];
+                    r[c] = h[c];
+                    r[3 + c] = l[c];
                 }
             }
             __syncthreads();
+            // ... the splits folded with FP32 two-sums in order, widened once
             if (owner) {
-                ax = (double)s_hl[tid][0] + (double)s_hl[tid][3];
-                ay = (double)s_hl[tid][1] + (double)s_hl[tid][4];
-                az = (double)s_hl[tid][2] + (double)s_hl[tid][5];
+                float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+                for (int q = 0; q < Q; ++q) {
+                    const float *r = s_red + 6 * (q * spad + tid);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float sum, err;
+                        two_sum(h[c], r[c], sum, err);
+                        h[c] = sum;
+                        l[c] = __fadd_rn(l[c], __fadd_rn(r[3 + c], err));
+                    }
+                }
+                ax = (double)h[0] + (double)l[0];
+                ay = (double)h[1] + (double)l[1];
+                az = (double)h[2] + (double)l[2];
             }
         }
         const bool last_kick = a.kdk && t == a.steps;  // the closing half kick of KDK

@@ -73,11 +73,10 @@ cudaError_t measure_peaks(int blocks, float *sink, cudaStream_t st, double out[3
 // or the precision form.
 constexpr int64_t kClusterMaxN = 4096;      // two replicas of 64 KiB
 // Untuned, the cluster path serves systems up to these sizes. Measured on
-// GB300 at 100 steps, us per step cluster vs graph: FP32 1.9 vs 5.2 at
-// N = 256, 3.5 vs 5.7 at 512, 9.6 vs 5.9 at 1024 (the graph path's 152 SMs
-// outrun one cluster's 16); precision form 3.3 vs 8.5 at 256, 10.8 vs 10.9
-// at 1024, 21.2 vs 13.2 at 2048 (its graph path's FP64 update per step
-// costs more at small N).
+// GB300 at 100 steps, us per step cluster vs graph: FP32 1.9 vs 4.7 at
+// N = 256, 2.5 vs 4.9 at 512, 6.1 vs 5.5 at 1024 (the graph path's 152 SMs
+// outrun one cluster's 16 from there on); precision form 3.1 vs 8.4 at 256,
+// 7.4 vs 10.8 at 1024, 21.9 vs 13.3 at 2048.
 constexpr int64_t kClusterDefaultN = 512;
 constexpr int64_t kClusterDefaultN64 = 1024;
 // Cluster size (16, or 8 where 16 cannot be scheduled) for n bodies; 0 if

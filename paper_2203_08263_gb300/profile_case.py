@@ -1,6 +1,7 @@
 """Run one pair-sum kernel on a fixed launch shape, for timing and profiling.
 
     python -m paper_2203_08263_gb300.profile_case --n 65536 --shape 128,4,16,256 --pol fp32
+    python -m paper_2203_08263_gb300.profile_case --n 1024 --pol step --steps 100 --path 2
     python -m paper_2203_08263_gb300.profile_case --peaks
 
 Input: Plummer sphere (seed 1), eps = 0.05. Prints the CUDA-event time per
@@ -22,13 +23,17 @@ def main():
     ap.add_argument("--pol", default="fp32",
                     choices=["fp32", "comp", "vjp", "vjp-comp", "energy", "step", "step-comp"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1, help="paper steps per call for --pol step / step-comp")
+    ap.add_argument("--path", type=int, default=0,
+                    help="nb_run path for --pol step / step-comp: 0 chosen per size, 1 graph, 2 one cluster")
     ap.add_argument("--peaks", action="store_true")
     a = ap.parse_args()
 
     import torch
 
     from paper_2203_08263_gb300 import build, ics
-    from paper_2203_08263_gb300.nbody import MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, Context
+    from paper_2203_08263_gb300.nbody import (MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, NB_DBG_RUN_PATH,
+                                              Context)
 
     build.build()
     if a.peaks:
@@ -42,6 +47,7 @@ def main():
     dev = torch.device("cuda:0")
     s = ics.plummer(a.n, seed=1)
     ctx = Context(1.0, 0.05, 1e-3, precision=prec, tile_override=shape)
+    ctx.debug_set(NB_DBG_RUN_PATH, a.path)
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,
@@ -53,7 +59,7 @@ def main():
         elif a.pol in ("vjp", "vjp-comp"):
             ctx.vjp(x, m, ab)
         elif a.pol in ("step", "step-comp"):
-            ctx.run(x, v, m, 1)  # one paper step: pack + force sum with the kick/drift epilogue
+            ctx.run(x, v, m, a.steps)  # paper steps: pack + force sums with the kick/drift epilogue
         else:
             ctx.energy(x, v, m)
 
@@ -69,7 +75,7 @@ def main():
         times.append(e0.elapsed_time(e1) / 1e3)
     ctx.sync()
     t = min(times)
-    inter = float(a.n) ** 2
+    inter = float(a.n) ** 2 * (a.steps if a.pol in ("step", "step-comp") else 1)
     print(json.dumps({"n": a.n, "pol": a.pol, "shape": ctx.get_config(a.n, mode), "s": t, "times": times,
                       "interactions_per_s": inter / t, "tflops_20": 20 * inter / t / 1e12}))
 
