@@ -386,7 +386,7 @@ def extras(ctx0, torch, dev, np):
     c = Context(1.0, 0.01, 1e-3, device=dev.index)
     xb, vb, mb = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (bx, bv, bm))
     offt = torch.tensor(off, dtype=torch.int64)
-    c.autotune_batched(offt)  # tile / gang shape from the project's tuner
+    c.autotune_batched(offt)  # threads, bodies per thread and j-tile from the project's tuner
     c.run_batched(offt, xb.clone(), vb.clone(), mb, 1)  # plan + capture
     t = _timed(torch, dev, lambda: c.run_batched(offt, xb, vb, mb, 100))
     sizes = np.diff(off).astype(np.float64)

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
                 const unsigned id = h_id[low];
                 h_id[low] = kNoItem;
                 --nheld;
-                atomicOr(a.err, kErrGang);
+                atomicOr(a.err, kErrStepDep);
                 abort = true;
                 return id;
             }

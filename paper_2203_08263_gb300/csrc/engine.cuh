@@ -56,7 +56,7 @@ enum ErrBits : int {
     kErrFullWait = 1,   // consumer gave up waiting for a tile
     kErrEmptyWait = 2,  // producer gave up waiting for a free slot
     kErrDrain = 4,      // producer gave up waiting for its own copies
-    kErrGang = 8,       // batched kernel: wait for a previous step gave up
+    kErrStepDep = 8,    // batched kernel: a system's previous step did not finish in time
 };
 
 enum DebugBits : int {
