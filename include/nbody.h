@@ -118,13 +118,15 @@ nb_status nb_step(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, void 
 
 /*
  * `steps` steps in place on x, v (Section 3.1's loop over the update), by one
- * of two paths with the same arithmetic: a CUDA graph of one force launch per
- * step that the context captures once per (n, buffers, steps, checkpoint
- * layout) and caches; or, for systems of at most 4096 bodies, one kernel on
- * one thread-block cluster that keeps the positions in distributed shared
- * memory across all steps. nb_autotune picks the faster path per size;
- * untuned, the cluster path serves n <= 512 (FP32) or n <= 1024 (precision
- * form). ckpt (nullable, device):
+ * of three paths with the same arithmetic: a CUDA graph of one force launch
+ * per step that the context captures once per (n, buffers, steps, checkpoint
+ * layout) and caches; for systems of at most 4096 bodies, one kernel on one
+ * thread-block cluster that keeps the positions in distributed shared memory
+ * across all steps; for at most 8192 bodies, the same kernel on a cooperative
+ * grid of up to one CTA per SM, exchanging positions through L2 with a
+ * bounded grid barrier per step. nb_autotune picks the fastest path per size;
+ * untuned, the cluster path serves n <= 512, the grid form n <= 4096 (FP32)
+ * or n <= 8192 (precision form), and the graph path the rest. ckpt (nullable, device):
  * [steps/ckpt_every + 1][n][6] in the state type; slot k receives (x, v)
  * after k*ckpt_every steps (slot 0 = the input state). ckpt_every must divide
  * steps when ckpt != NULL. The paper scheme only when checkpointing.
@@ -214,7 +216,7 @@ nb_status nb_energy(nb_ctx *ctx, int64_t n, const void *x, const void *v, const 
  * Time the candidate kernel shapes for problems of size n in mode `mode`
  * (0 = forward, 1 = adjoint VJP) and store the fastest in the context's
  * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). In
- * mode 0 with n <= 4096 it also times nb_run's two paths
+ * mode 0 with n <= 8192 it also times nb_run's paths
  * (graph of force launches, one-cluster kernel) and records the faster. Calls
  * that find no entry for their size bucket use a built-in heuristic instead.
  * Synchronous.
@@ -238,9 +240,11 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * many nanoseconds (default 2e9; 0 gives up at the first poll that returns
  * without the phase complete). NB_DBG_STALL_PRODUCER (value 0/1): the
  * pair-sum kernels issue no j-tile copies, so every tile wait of nb_accel,
- * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out; with a short
- * timeout this exercises the error path without hanging (results are then
- * invalid and nb_sync returns NB_ERR_TIMEOUT). */
+ * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out, and in
+ * nb_run's grid form CTA 0 never arrives at the step barrier, so every
+ * barrier wait runs out; with a short timeout this exercises the error path
+ * without hanging (results are then invalid and nb_sync returns
+ * NB_ERR_TIMEOUT). */
 typedef enum {
     NB_DBG_WAIT_TIMEOUT_NS = 1,
     NB_DBG_STALL_PRODUCER = 2,
@@ -250,8 +254,8 @@ typedef enum {
      * 2 = powf(s, -1.5). Tuned shapes apply to 0 only. */
     NB_DBG_MATH_VARIANT = 3,
     /* nb_run path: 0 = chosen per size (default), 1 = graph of force
-     * launches, 2 = one-cluster kernel (NB_ERR_UNSUPPORTED at nb_run when
-     * the system does not qualify). */
+     * launches, 2 = one-cluster kernel, 3 = its grid form
+     * (NB_ERR_UNSUPPORTED at nb_run when the system does not qualify). */
     NB_DBG_RUN_PATH = 4
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);

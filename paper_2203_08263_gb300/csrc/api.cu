@@ -83,7 +83,7 @@ void nb_destroy(nb_ctx *ctx) {
                       &ctx->tune[3],   &ctx->tune[4],   &ctx->tune[5],    &ctx->bat,
                       &ctx->adj_traj[0], &ctx->adj_traj[1], &ctx->adj_traj64[0],
                       &ctx->adj_traj64[1], &ctx->adj_x[0], &ctx->adj_x[1], &ctx->adj_v[0],
-                      &ctx->adj_v[1],  &ctx->part2,     &ctx->counters2};
+                      &ctx->adj_v[1],  &ctx->part2,     &ctx->counters2,  &ctx->gridbar};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->err_word) cudaFree(ctx->err_word);
@@ -244,7 +244,7 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         return NB_OK;
     }
     if (key == NB_DBG_RUN_PATH) {
-        if (value < 0 || value > 2) return fail(ctx, NB_ERR_INVALID, "run path must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(ctx, NB_ERR_INVALID, "run path must be 0, 1, 2 or 3");
         ctx->run_path = (int)value;
         return NB_OK;
     }

@@ -104,22 +104,24 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     NB_TRY(sync_and_check(ctx, st));
     ctx->tuned[tune_key(ctx, mode, n)] = best;
     clear_graphs(ctx);
-    // nb_run's two paths for small systems: the graph of force launches
-    // (with the shape just chosen) against the one-cluster kernel, 20 steps
+    // nb_run's paths for small systems: the graph of force launches (with the
+    // shape just chosen), the one-cluster kernel and its grid form, 20 steps
     // each on zeroed state (timing does not depend on the values)
-    int cluster = 0;
     const bool f64 = f64_state(ctx);
-    if (mode == 0 && (f64 || ctx->math == 0) && n <= kClusterMaxN) cluster = cluster_run_size(n, f64);
-    if (cluster) {
+    const bool fused = mode == 0 && (f64 || ctx->math == 0);
+    const int cluster = fused && n <= kClusterMaxN ? cluster_run_size(n, f64) : 0;
+    const int grid = fused ? grid_run_ctas(n, ctx->num_sms) : 0;
+    if (cluster || grid) {
         void *x = ctx->tune[1].p, *v = ctx->tune[4].p, *m = ctx->tune[3].p;
         NB_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 3 * esize(ctx), st));
         NB_CUDA(cudaMemsetAsync(v, 0, (size_t)n * 3 * esize(ctx), st));
         NB_CUDA(cudaMemsetAsync(m, 0, (size_t)n * esize(ctx), st));
         const int steps = 20;
         const int saved_path = ctx->run_path;
-        float ms_path[2] = {1e30f, 1e30f};
+        float ms_path[3] = {1e30f, 1e30f, 1e30f};
         nb_status rs = NB_OK;
-        for (int path = 1; path <= 2 && rs == NB_OK; ++path) {
+        for (int path = 1; path <= 3 && rs == NB_OK; ++path) {
+            if ((path == 2 && !cluster) || (path == 3 && !grid)) continue;
             ctx->run_path = path;
             rs = run_device(ctx, n, x, v, m, steps, nullptr, 0, st);  // warm-up (and graph capture)
             for (int rep = 0; rs == NB_OK && rep < 3; ++rep) {
@@ -137,8 +139,11 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
         ctx->run_path = saved_path;
         NB_TRY(rs);
         NB_TRY(sync_and_check(ctx, st));
+        int best_path = 0;  // 0 graph, 1 one cluster, 2 grid
+        for (int k = 1; k < 3; ++k)
+            if (ms_path[k] < ms_path[best_path]) best_path = k;
         ctx->tuned[tune_key(ctx, mode, n) + "|run"] =
-            TuneEntry{ms_path[1] < ms_path[0] ? 1 : 0, cluster, 0, 0, 0};
+            TuneEntry{best_path, best_path == 1 ? cluster : (best_path == 2 ? grid : 0), 0, 0, 0};
         clear_graphs(ctx);
     }
     save_tune_file(ctx);

@@ -13,6 +13,7 @@
 // separates the steps: at N of a few thousand the graph path's per-step
 // launch, bulk-copy and split-reduction latencies dominate, and this path
 // removes them.
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 
@@ -32,7 +33,49 @@ struct ClusterArgs {
     const void *m;       // [n] in the state type
     void *ckpt;          // nullable: slots of [n][6] (x, v), slot s after step s * ckpt_every
     int ckpt_every;
+    // grid form only
+    float4 *xm0, *xm1;   // packed positions in global memory, [npad] each, double-buffered
+    unsigned *bar;       // grid barrier: arrivals, cumulative over the launch (zeroed before it)
+    int *err;
+    uint64_t timeout_ns;
+    int stall;           // timeout tests: CTA 0 never arrives, so every barrier wait runs out
 };
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of the grid form (all CTAs resident: cooperative
+// launch). Arrivals accumulate over the launch; barrier number `epoch`
+// completes when epoch x gridDim.x CTAs have arrived. Bounded: after
+// timeout_ns the CTA records an error and returns false (it then leaves the
+// step loop, so the others give up at their next barrier too).
+__device__ __forceinline__ bool grid_barrier(const ClusterArgs &a, unsigned epoch, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the writers fenced their records before the __syncthreads
+        if (!(a.stall && blockIdx.x == 0)) atomicAdd(a.bar, 1u);
+        const unsigned target = epoch * gridDim.x;
+        int ok = 1;
+        if (ld_relaxed_gpu(a.bar) < target) {
+            const uint64_t t0 = global_ns();
+            while (ld_relaxed_gpu(a.bar) < target) {
+                __nanosleep(32);
+                if (global_ns() - t0 > a.timeout_ns) {
+                    atomicOr(a.err, kErrStepDep);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // the others' records after it
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
@@ -76,17 +119,23 @@ constexpr int kCompBlockPairs = 32;
 // F64 = false: FP32 state and forces (AccelF32x2). F64 = true: the precision
 // form, FP64 state, FP32 pair terms summed in blocks, two-sums across blocks,
 // FP64 across lanes and in the update (AccelComp's arithmetic).
-template <int NT, bool F64>
+// GRID = false: one thread-block cluster, replicas exchanged through
+// distributed shared memory. GRID = true: a cooperative grid of up to one CTA
+// per SM; each step every CTA writes its slice's records to a global buffer,
+// meets the others at a grid barrier and reloads all records into its shared
+// memory.
+template <int NT, bool F64, bool GRID>
 __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a) {
     using TS = typename std::conditional<F64, double, float>::type;
-    extern __shared__ __align__(16) float4 rep[];  // [2][npad] packed pair records
+    extern __shared__ __align__(16) float4 rep[];  // cluster: [2][npad]; grid: [npad]
     const TS *xg = reinterpret_cast<const TS *>(a.x);
     const TS *vg = reinterpret_cast<const TS *>(a.v);
     const TS *mg = reinterpret_cast<const TS *>(a.m);
     TS *ckpt = reinterpret_cast<TS *>(a.ckpt);
     const int tid = threadIdx.x;
-    const uint32_t rank = cluster_ctarank();
-    const uint32_t csize = cluster_nctarank();
+    const uint32_t rank = GRID ? blockIdx.x : cluster_ctarank();
+    const uint32_t csize = GRID ? gridDim.x : cluster_nctarank();
+    __shared__ int s_ok;
     const int S = a.slice;
     const int npad = a.npad;
     // Thread mapping of the force sum: lane l of warp w sums body
@@ -107,13 +156,24 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
     const int io = (int)rank * S + tid;
     const bool owner = tid < S && io < a.n;
     __shared__ float s_red[NT * (F64 ? 6 : 3)];  // per (split, body): partial sums (hi, lo)
-    // both replicas: every body's record in buffer 0, zeros in buffer 1
-    for (int k = tid; k < npad; k += NT) {
+    if constexpr (!GRID) {
+        // both replicas: every body's record in buffer 0, zeros in buffer 1
+        for (int k = tid; k < npad; k += NT) {
+            if (k < a.n)
+                pair_put(rep, k, (float)xg[3 * k], (float)xg[3 * k + 1], (float)xg[3 * k + 2], (float)mg[k]);
+            else
+                pair_put(rep, k, 0.f, 0.f, 0.f, 0.f);
+            pair_put(rep + npad, k, 0.f, 0.f, 0.f, 0.f);
+        }
+    } else if (tid < S) {
+        // this CTA's slice of both global buffers: records (zeros past n)
+        const int k = (int)rank * S + tid;
         if (k < a.n)
-            pair_put(rep, k, (float)xg[3 * k], (float)xg[3 * k + 1], (float)xg[3 * k + 2], (float)mg[k]);
+            pair_put(a.xm0, k, (float)xg[3 * k], (float)xg[3 * k + 1], (float)xg[3 * k + 2], (float)mg[k]);
         else
-            pair_put(rep, k, 0.f, 0.f, 0.f, 0.f);
-        pair_put(rep + npad, k, 0.f, 0.f, 0.f, 0.f);
+            pair_put(a.xm0, k, 0.f, 0.f, 0.f, 0.f);
+        pair_put(a.xm1, k, 0.f, 0.f, 0.f, 0.f);
+        __threadfence();  // these records before the CTA's arrival at the barrier
     }
     TS xs[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
     float mi = 0.f;
@@ -131,13 +191,26 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
         }
     }
     // no CTA writes into another's buffer 1 before that one has zeroed it
-    cluster_barrier();
+    // (grid: no CTA reads buffer 0 before every slice of it is written)
+    bool ok = true;
+    if constexpr (GRID) ok = grid_barrier(a, 1u, &s_ok);
+    else cluster_barrier();
 
     const int evals = a.steps + (a.kdk && a.steps > 0 ? 1 : 0);
     int cur = 0;
-    for (int t = 0; t < evals; ++t) {
-        const float4 *src = rep + cur * npad;
-        float4 *dst = rep + (cur ^ 1) * npad;
+    for (int t = 0; ok && t < evals; ++t) {
+        const float4 *src;
+        float4 *dst;
+        if constexpr (GRID) {
+            const float4 *g = cur ? a.xm1 : a.xm0;
+            for (int k = tid; k < npad; k += NT) rep[k] = __ldcg(g + k);  // all records, from L2
+            __syncthreads();
+            src = rep;
+            dst = cur ? a.xm0 : a.xm1;
+        } else {
+            src = rep + cur * npad;
+            dst = rep + (cur ^ 1) * npad;
+        }
         TS ax = 0, ay = 0, az = 0;
         AccelF32x2::I ist;
         AccelF32x2::C cst;
@@ -243,6 +316,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
             }
             if (!last_kick) {
                 pair_put(dst, io, (float)xs[0], (float)xs[1], (float)xs[2], mi);
+                if constexpr (GRID) __threadfence();  // the record before the CTA's arrival
                 if (ckpt && (t + 1) % a.ckpt_every == 0) {
                     TS *ck = ckpt + (int64_t)((t + 1) / a.ckpt_every) * 6 * a.n + 6 * (int64_t)io;
                     ck[0] = xs[0]; ck[1] = xs[1]; ck[2] = xs[2];
@@ -251,16 +325,21 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
             }
         }
         if (last_kick) break;
-        __syncthreads();  // this CTA's slice of dst is complete
-        // The slice of S bodies is float4 [rank*S, rank*S + S) of the pair
-        // layout (S even): copy it into the same place of every other CTA.
-        const int base = (int)rank * S;
-        for (int q = tid; q < (int)(csize - 1) * S; q += NT) {
-            const uint32_t to = (rank + 1 + (uint32_t)(q / S)) % csize;
-            const int k = base + q % S;
-            st_cluster_f4(map_to_rank(smem_addr(&dst[k]), to), dst[k]);
+        if constexpr (GRID) {
+            // every slice of dst written (global) before anyone reloads it
+            ok = grid_barrier(a, (unsigned)t + 2u, &s_ok);
+        } else {
+            __syncthreads();  // this CTA's slice of dst is complete
+            // The slice of S bodies is float4 [rank*S, rank*S + S) of the pair
+            // layout (S even): copy it into the same place of every other CTA.
+            const int base = (int)rank * S;
+            for (int q = tid; q < (int)(csize - 1) * S; q += NT) {
+                const uint32_t to = (rank + 1 + (uint32_t)(q / S)) % csize;
+                const int k = base + q % S;
+                st_cluster_f4(map_to_rank(smem_addr(&dst[k]), to), dst[k]);
+            }
+            cluster_barrier();
         }
-        cluster_barrier();
         cur ^= 1;
     }
     if (owner) {
@@ -283,14 +362,17 @@ constexpr int kClusterThreads = 512;
 // replicas must fit in shared memory.
 using ClusterFn = void (*)(const ClusterArgs);
 
-ClusterFn cluster_fn(bool f64) {
-    return f64 ? cluster_run_kernel<kClusterThreads, true> : cluster_run_kernel<kClusterThreads, false>;
+ClusterFn cluster_fn(bool f64, bool grid) {
+    if (grid)
+        return f64 ? cluster_run_kernel<kClusterThreads, true, true>
+                   : cluster_run_kernel<kClusterThreads, false, true>;
+    return f64 ? cluster_run_kernel<kClusterThreads, true, false>
+               : cluster_run_kernel<kClusterThreads, false, false>;
 }
 
 int cluster_run_size(int64_t n, bool f64) {
     if (n <= 0 || n > kClusterMaxN) return 0;
-    ClusterFn fn = cluster_fn(f64);
-    for (int c : {16, 8}) {
+    ClusterFn fn = cluster_fn(f64, false);    for (int c : {16, 8}) {
         const int64_t slice = ((n + c - 1) / c + 1) / 2 * 2;
         if (slice > kClusterThreads) continue;
         const size_t smem = (size_t)2 * c * slice * 16;
@@ -323,7 +405,7 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
                                int steps, int kdk, float eps2, double G, double dt, void *ckpt,
                                int ckpt_every, cudaStream_t st) {
     if (cluster <= 0 || n <= 0 || n > kClusterMaxN) return cudaErrorInvalidValue;
-    ClusterFn fn = cluster_fn(f64);
+    ClusterFn fn = cluster_fn(f64, false);
     ClusterArgs a;
     a.n = (int)n;
     a.slice = (int)(((n + cluster - 1) / cluster + 1) / 2 * 2);
@@ -338,6 +420,11 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
     a.m = m;
     a.ckpt = ckpt;
     a.ckpt_every = ckpt_every > 0 ? ckpt_every : 1;
+    a.xm0 = a.xm1 = nullptr;
+    a.bar = nullptr;
+    a.err = nullptr;
+    a.timeout_ns = 0;
+    a.stall = 0;
     const size_t smem = (size_t)2 * a.npad * 16;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -356,6 +443,61 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
     attr[0].val.clusterDim.x = (unsigned)cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+// Grid form: CTAs for n bodies (slices of 2 * ceil(n / 32 / 2) bodies and
+// at most one CTA per SM), 0 if the path cannot run n bodies here.
+int grid_run_ctas(int64_t n, int num_sms) {
+    if (n <= 0 || n > kGridMaxN) return 0;
+    int64_t slice = std::max<int64_t>(16, ((n + num_sms - 1) / num_sms + 1) / 2 * 2);
+    if (slice > kClusterThreads) return 0;
+    return (int)((n + slice - 1) / slice);
+}
+
+cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, const void *m, int steps,
+                            int kdk, float eps2, double G, double dt, void *ckpt, int ckpt_every,
+                            float4 *xm0, float4 *xm1, unsigned *bar, int *err, uint64_t timeout_ns,
+                            int stall, cudaStream_t st) {
+    if (ctas <= 0 || n <= 0 || n > kGridMaxN) return cudaErrorInvalidValue;
+    ClusterFn fn = cluster_fn(f64, true);
+    ClusterArgs a;
+    a.n = (int)n;
+    a.slice = (int)(((n + ctas - 1) / ctas + 1) / 2 * 2);
+    if (a.slice > kClusterThreads) return cudaErrorInvalidValue;
+    a.npad = ctas * a.slice;
+    a.steps = steps;
+    a.kdk = kdk;
+    a.eps2 = eps2;
+    a.G = G;
+    a.dt = dt;
+    a.x = x;
+    a.v = v;
+    a.m = m;
+    a.ckpt = ckpt;
+    a.ckpt_every = ckpt_every > 0 ? ckpt_every : 1;
+    a.xm0 = xm0;
+    a.xm1 = xm1;
+    a.bar = bar;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    a.stall = stall;
+    const size_t smem = (size_t)a.npad * 16;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, a);

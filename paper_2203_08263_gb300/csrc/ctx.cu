@@ -317,12 +317,14 @@ void graph_insert(nb_ctx *ctx, const std::string &key, cudaGraphExec_t ex, int64
 
 // ------------------------------------------------------- device run path
 
-nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
-    *cluster = 0;
+nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *path, int *size) {
+    *path = 1;
+    *size = 0;
     if (ctx->run_path == 1) return NB_OK;
-    int c = 0;
     const bool f64 = f64_state(ctx);
-    if ((f64 || ctx->math == 0) && n <= kClusterMaxN) {
+    const bool eligible = f64 || ctx->math == 0;  // the math-variant ablation has no fused form
+    int c = 0, g = 0;
+    if (eligible && n <= kClusterMaxN) {
         const int64_t key = 2 * n + (f64 ? 1 : 0);
         auto it = ctx->cluster_sizes.find(key);
         if (it == ctx->cluster_sizes.end()) {
@@ -332,34 +334,60 @@ nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster) {
             c = it->second;
         }
     }
-    if (ctx->run_path == 2) {
-        if (!c)
+    if (eligible) g = grid_run_ctas(n, ctx->num_sms);
+    if (ctx->run_path == 2 || ctx->run_path == 3) {
+        const int want = ctx->run_path == 2 ? c : g;
+        if (!want)
             return fail(ctx, NB_ERR_UNSUPPORTED,
-                        "the one-cluster path runs systems of at most %lld bodies (FP32 with the "
-                        "MUFU denominator, or the precision form) that fit a cluster on this device",
-                        (long long)kClusterMaxN);
-        *cluster = c;
+                        "the %s path runs systems of at most %lld bodies (FP32 with the MUFU "
+                        "denominator, or the precision form)%s",
+                        ctx->run_path == 2 ? "one-cluster" : "grid",
+                        (long long)(ctx->run_path == 2 ? kClusterMaxN : kGridMaxN),
+                        ctx->run_path == 2 ? " that fit a cluster on this device" : "");
+        *path = ctx->run_path;
+        *size = want;
         return NB_OK;
     }
-    if (!c) return NB_OK;
     auto t = ctx->tuned.find(tune_key(ctx, 0, n) + "|run");
-    if (t != ctx->tuned.end())
-        *cluster = t->second.pol ? c : 0;
-    else
-        *cluster = n <= (f64 ? kClusterDefaultN64 : kClusterDefaultN) ? c : 0;
+    if (t != ctx->tuned.end()) {
+        // tuned: 0 graph, 1 one cluster, 2 grid (a choice this device cannot run falls back)
+        if (t->second.pol == 1 && c) { *path = 2; *size = c; }
+        if (t->second.pol == 2 && g) { *path = 3; *size = g; }
+        return NB_OK;
+    }
+    if (c && n <= (f64 ? kClusterDefaultN64 : kClusterDefaultN)) {
+        *path = 2;
+        *size = c;
+    } else if (g && n <= (f64 ? kGridDefaultN64 : kGridDefaultN)) {
+        *path = 3;
+        *size = g;
+    }
     return NB_OK;
 }
 
 nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
                      void *ckpt, int ckpt_every, cudaStream_t st) {
-    int cluster = 0;
-    NB_TRY(choose_run_path(ctx, n, &cluster));
-    if (cluster) {
-        NB_CUDA(launch_cluster_run(cluster, n, f64_state(ctx), x, v, m, steps,
-                                   ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0,
-                                   (float)(ctx->p.eps * ctx->p.eps), ctx->p.G, ctx->p.dt, ckpt,
-                                   ckpt_every, st));
+    int path = 1, size = 0;
+    NB_TRY(choose_run_path(ctx, n, &path, &size));
+    const int kdk_flag = ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0;
+    const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
+    if (path == 2) {
+        NB_CUDA(launch_cluster_run(size, n, f64_state(ctx), x, v, m, steps, kdk_flag, eps2, ctx->p.G,
+                                   ctx->p.dt, ckpt, ckpt_every, st));
         ctx->launches += 1;
+        return NB_OK;
+    }
+    if (path == 3) {
+        const int64_t slice = ((n + size - 1) / size + 1) / 2 * 2;
+        const size_t bytes = (size_t)size * slice * 16;
+        NB_TRY(ensure(ctx, ctx->xm[0], bytes));
+        NB_TRY(ensure(ctx, ctx->xm[1], bytes));
+        NB_TRY(ensure(ctx, ctx->gridbar, 256));
+        NB_CUDA(launch_grid_run(size, n, f64_state(ctx), x, v, m, steps, kdk_flag, eps2, ctx->p.G,
+                                ctx->p.dt, ckpt, ckpt_every, (float4 *)ctx->xm[0].p,
+                                (float4 *)ctx->xm[1].p, (unsigned *)ctx->gridbar.p, ctx->err_word,
+                                ctx->timeout_ns, (ctx->debug & kDbgStallProducer) ? 1 : 0, st));
+        ctx->launches += 2;  // the counter reset and the kernel
         return NB_OK;
     }
     Shape s;

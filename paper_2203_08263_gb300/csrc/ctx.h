@@ -44,7 +44,8 @@ struct nb_ctx {
     int *err_word = nullptr;
     // scratch
     DevBuf xm[2], rec, part, counters, vals, red, st_v, abar64, stage[4], tune[6];
-    DevBuf bat;  // batched-kernel scratch
+    DevBuf bat;      // batched-kernel scratch
+    DevBuf gridbar;  // grid form of the step loop: barrier counter
     // adjoint: ping-pong segment buffers and the recompute stream's split scratch
     DevBuf adj_traj[2], adj_traj64[2], adj_x[2], adj_v[2], part2, counters2;
     std::map<std::string, nb::detail::GraphEntry> graphs;
@@ -52,7 +53,7 @@ struct nb_ctx {
     uint64_t timeout_ns = 2000000000ull;
     int debug = 0;
     int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
-    int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one-cluster kernel
+    int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one cluster, 3 grid
     std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;
@@ -123,9 +124,10 @@ nb_status pack(nb_ctx *ctx, int64_t n, int64_t npad, const void *x, const void *
                float4 *xm, void *ckpt0, cudaStream_t st);
 GraphEntry *graph_lookup(nb_ctx *ctx, const std::string &key);
 void graph_insert(nb_ctx *ctx, const std::string &key, cudaGraphExec_t ex, int64_t nodes);
-// Which nb_run path serves n bodies: *cluster = the cluster size of the
-// one-cluster kernel, or 0 for the graph of force launches.
-nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *cluster);
+// Which nb_run path serves n bodies: *path = 1 graph of force launches,
+// 2 one-cluster kernel, 3 grid form of it; *size = the cluster size or the
+// grid's CTAs.
+nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *path, int *size);
 nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int steps,
                      void *ckpt, int ckpt_every, cudaStream_t st);
 nb_status accel_device(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a_out,

@@ -72,13 +72,18 @@ cudaError_t measure_peaks(int blocks, float *sink, cudaStream_t st, double out[3
 // thread-block cluster and exchanged through distributed shared memory; FP32
 // or the precision form.
 constexpr int64_t kClusterMaxN = 4096;      // two replicas of 64 KiB
-// Untuned, the cluster path serves systems up to these sizes. Measured on
-// GB300 at 100 steps, us per step cluster vs graph: FP32 1.9 vs 4.7 at
-// N = 256, 2.5 vs 4.9 at 512, 6.1 vs 5.5 at 1024 (the graph path's 152 SMs
-// outrun one cluster's 16 from there on); precision form 3.1 vs 8.4 at 256,
-// 7.4 vs 10.8 at 1024, 21.9 vs 13.3 at 2048.
+// Untuned choice of nb_run's path (one cluster up to kClusterDefault*, the
+// grid form up to kGridDefault*, the graph of force launches above).
+// Measured on GB300 at 100 steps, us per step graph / one cluster / grid:
+//   FP32            N = 256: 4.6 / 1.9 / 2.9     1024: 5.6 / 6.1 / 4.4
+//                   N = 4096: 12.8 / 74 / 10.8    8192: 33.8 / - / 33.5
+//   precision form  N = 256: 8.6 / 3.1 / 4.2     1024: 10.8 / 7.3 / 5.8
+//                   N = 4096: 24.2 / 80 / 12.7    8192: 44.4 / - / 37.1
+// (one cluster has 16 SMs; the grid form all 152 but pays a grid barrier and
+// an L2 reload per step; the graph path pays a kernel boundary and, in the
+// precision form, an FP64 update spread over few CTAs.)
 constexpr int64_t kClusterDefaultN = 512;
-constexpr int64_t kClusterDefaultN64 = 1024;
+constexpr int64_t kClusterDefaultN64 = 512;
 // Cluster size (16, or 8 where 16 cannot be scheduled) for n bodies; 0 if
 // the path cannot run n bodies on this device.
 // f64: the precision form (FP64 state, compensated FP32 forces).
@@ -86,5 +91,17 @@ int cluster_run_size(int64_t n, bool f64);
 cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *v, const void *m,
                                int steps, int kdk, float eps2, double G, double dt, void *ckpt,
                                int ckpt_every, cudaStream_t st);
+// The same step loop on a cooperative grid of up to one CTA per SM: slices
+// written to a global double buffer (xm0, xm1: [npad] records each, npad =
+// ctas x slice), a bounded grid barrier per step (bar: one counter, zeroed
+// by the launch), all records reloaded into shared memory.
+constexpr int64_t kGridMaxN = 8192;  // one replica of 128 KiB
+constexpr int64_t kGridDefaultN = 4096;
+constexpr int64_t kGridDefaultN64 = 8192;
+int grid_run_ctas(int64_t n, int num_sms);
+cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, const void *m, int steps,
+                            int kdk, float eps2, double G, double dt, void *ckpt, int ckpt_every,
+                            float4 *xm0, float4 *xm1, unsigned *bar, int *err, uint64_t timeout_ns,
+                            int stall, cudaStream_t st);
 
 }  // namespace nb
