@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
     // v), and the repacked position written to the other buffer. A generic
     // lambda, instantiated for each R the kernel holds.
     auto run_item = [&](auto r_const, const float4 *src, float4 *dst, int64_t b0, int64_t lo,
-                        int64_t hi, int ntl) {
+                        int64_t hi, int ntl, int last_pairs) {
         constexpr int R = decltype(r_const)::value;
         AccelF32x2::I ist[R];
         AccelF32x2::T tot[R];
@@ -232,8 +232,11 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
             }
             if (!give_up) {
                 const float4 *tile = ring + slot * f4_per_tile;
+                // the system's last tile: only its real records (the rest are
+                // zero-mass padding and would add exactly 0)
+                const int jpairs = q == ntl - 1 ? last_pairs : (a.jt >> 1);
 #pragma unroll(AccelF32x2::UNROLL)
-                for (int jp = 0; jp < (a.jt >> 1); ++jp) {
+                for (int jp = 0; jp < jpairs; ++jp) {
                     float4 rec[2] = {tile[2 * jp], tile[2 * jp + 1]};
 #pragma unroll
                     for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
@@ -303,20 +306,21 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
         const int64_t n = a.off[s + 1] - b0;
         const int64_t p0 = a.poff[s];
         const int ntl = (int)((n + a.jt - 1) / a.jt);
+        const int last_pairs = (int)((n - (int64_t)(ntl - 1) * a.jt + 1) >> 1);
         const int64_t hi = lo + (int64_t)NT * r < n ? lo + (int64_t)NT * r : n;
         const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + p0;  // one float4 per body
         float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
         if (!s_abort && !give_up) {
             if constexpr (RMAX >= 8) {
-                if (r == 8) run_item(std::integral_constant<int, 8>{}, src, dst, b0, lo, hi, ntl);
+                if (r == 8) run_item(std::integral_constant<int, 8>{}, src, dst, b0, lo, hi, ntl, last_pairs);
             }
             if constexpr (RMAX >= 4) {
-                if (r == 4) run_item(std::integral_constant<int, 4>{}, src, dst, b0, lo, hi, ntl);
+                if (r == 4) run_item(std::integral_constant<int, 4>{}, src, dst, b0, lo, hi, ntl, last_pairs);
             }
             if constexpr (RMAX >= 2) {
-                if (r == 2) run_item(std::integral_constant<int, 2>{}, src, dst, b0, lo, hi, ntl);
+                if (r == 2) run_item(std::integral_constant<int, 2>{}, src, dst, b0, lo, hi, ntl, last_pairs);
             }
-            if (r == 1) run_item(std::integral_constant<int, 1>{}, src, dst, b0, lo, hi, ntl);
+            if (r == 1) run_item(std::integral_constant<int, 1>{}, src, dst, b0, lo, hi, ntl, last_pairs);
             fence_proxy_async_global();
         }
         __syncthreads();
