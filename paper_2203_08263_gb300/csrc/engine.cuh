@@ -168,7 +168,10 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int jpairs,
 
 // Register caps: 512 resident threads per SM at R <= 4 (<= 128 registers).
 // R = 8 stays uncapped: capping 128 x 8 tiles to 3 CTAs per SM (166
-// registers) measured 5 % slower than 2 CTAs at 210 registers.
+// registers) measured 5 % slower than 2 CTAs at 210 registers, and a 128 x 6
+// shape at 3 CTAs per SM (168 registers, no spills) 2-3 % slower at N = 2^18
+// and 10 % at 2^16: the reuse of each j-record across 8 i-bodies is worth
+// more than the extra resident warps.
 template <int NT, int R>
 constexpr int min_blocks() {
     return (NB_PRODUCER_WARP || R > 4) ? 1 : 512 / NT;
