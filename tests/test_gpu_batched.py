@@ -98,7 +98,7 @@ def test_c4_full_ensemble_sampled(nbm):
 
 
 # Sizes whose ragged rests need every item kind: rows of 128 i-bodies of
-# 1..8 (3 and 7 rounded up), a full chunk of 8 rows plus a rest, and tiny ones.
+# 1..8 (in binary: 3 = 2 + 1, 7 = 4 + 2 + 1), a full chunk of 8 rows plus a rest, and tiny ones.
 TAIL_SIZES = [1, 127, 128, 129, 300, 385, 640, 700, 896, 1000, 1024, 1025, 1500, 2047, 2200, 3]
 
 
