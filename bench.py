@@ -349,14 +349,16 @@ def extras(ctx0, torch, dev, np):
     from paper_2203_08263_gb300.nbody import Context
 
     out = {}
-    # C1: plain method, small: N = 1024 cube (seed 0), 10 steps in one graph
+    # C1: plain method, small: N = 1024 cube (seed 0), 10 steps through nb_run
+    # (the path the shipped tuning table picks: graph, one cluster or grid)
     s = ics.cube(1024, seed=0)
     c = Context(1.0, 0.01, 1e-3, device=dev.index)
     x, v, m = (torch.tensor(a, dtype=torch.float32, device=dev) for a in (s.x, s.v, s.m))
     c.run(x.clone(), v.clone(), m, 10)
     t = min(_timed(torch, dev, lambda: c.run(x, v, m, 10)) for _ in range(5))
     out["c1_small"] = {"n": 1024, "steps": 10, "s": t, "us_per_step": t / 10 * 1e6,
-                       "interactions_per_s": 1024.0 * 1024 * 10 / t, "shape": c.get_config(1024)}
+                       "interactions_per_s": 1024.0 * 1024 * 10 / t, "run_path": c.get_run_path(1024),
+                       "graph_path_shape": c.get_config(1024)}
     c.close()
     # C3: precision form, N = 2^20 Plummer (seed 2), FP64 state, 2 steps
     n = 1 << 20

@@ -228,6 +228,13 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode);
  * 1 if the shape came from a tuning run}. */
 nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5);
 
+/* The nb_run path the context would use for n bodies: out[0] = 1 graph of
+ * force launches, 2 one-cluster kernel, 3 its grid form; out[1] = the
+ * cluster size or the grid's CTAs (0 for the graph path); out[2] = 1 if the
+ * choice came from a tuning run. A query of this library's dispatch; the
+ * paper has no counterpart. */
+nb_status nb_get_run_path(nb_ctx *ctx, int64_t n, int *out3);
+
 /* Wait for the context's work on `stream`, then report (and clear) any error
  * recorded by a kernel: NB_ERR_TIMEOUT if a bounded wait gave up. */
 nb_status nb_sync(nb_ctx *ctx, void *stream);

@@ -150,6 +150,18 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     return NB_OK;
 }
 
+nb_status nb_get_run_path(nb_ctx *ctx, int64_t n, int *out3) {
+    if (!ctx || !out3) return NB_ERR_INVALID;
+    if (n <= 0) return fail(ctx, NB_ERR_INVALID, "n must be > 0");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    int path = 1, size = 0;
+    NB_TRY(choose_run_path(ctx, n, &path, &size));
+    out3[0] = path;
+    out3[1] = size;
+    out3[2] = ctx->run_path == 0 && ctx->tuned.count(tune_key(ctx, 0, n) + "|run") ? 1 : 0;
+    return NB_OK;
+}
+
 nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5) {
     if (!ctx || !out5) return NB_ERR_INVALID;
     if (mode < 0 || mode > 2) return fail(ctx, NB_ERR_INVALID, "mode must be 0, 1 or 2");

@@ -48,6 +48,7 @@ SIGNATURES = {
     "nb_autotune_batched": (_i, [_vp, _i, _vp]),
     "nb_get_batched_config": (_i, [_vp, _i, _vp, _c.POINTER(_i)]),
     "nb_set_batched_config": (_i, [_vp, _i, _vp, _i, _i, _i]),
+    "nb_get_run_path": (_i, [_vp, _i64, _c.POINTER(_i)]),
     "nb_adjoint": (_i, [_vp, _i64, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_vjp": (_i, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_energy": (_i, [_vp, _i64, _vp, _vp, _vp, _c.POINTER(_d), _vp]),
@@ -204,6 +205,12 @@ class Context:
                     "nb_get_batched_config")
         return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "items_per_step": out[3],
                 "ctas": out[4], "tuned": out[5] == 1, "pinned": out[5] == 2}
+
+    def get_run_path(self, n: int) -> dict:
+        """The nb_run path for n bodies: graph, cluster or grid, its size, and whether it was tuned."""
+        out = (_i * 3)()
+        self._check(self.lib.nb_get_run_path(self.h, int(n), out), "nb_get_run_path")
+        return {"path": {1: "graph", 2: "cluster", 3: "grid"}[out[0]], "size": out[1], "tuned": bool(out[2])}
 
     def set_batched_config(self, offsets, threads: int, bodies_per_thread: int, jtile: int):
         """Pin the batched shape for these sizes; (0, 0, 0) returns to the default."""

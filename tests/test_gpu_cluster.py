@@ -92,6 +92,9 @@ def test_default_path_choice(nbm):
     for n, launches in ((512, 1), (1024, 2), (4096, 2), (5000, 11)):
         s = ics.cube(n, seed=3)
         ctx = nbm.Context(1.0, 0.01, 1e-3)
+        want = "cluster" if n <= 512 else ("grid" if n <= 4096 else "graph")
+        rp = ctx.get_run_path(n)
+        assert rp["path"] == want and not rp["tuned"], (n, rp)
         x, v, m = _t(s.x), _t(s.v), _t(s.m)
         ctx.run(x, v, m, 10)
         ctx.sync()
@@ -106,6 +109,7 @@ def test_autotune_keeps_run_correct(nbm):
     s = ics.cube(n, seed=0)
     ctx = nbm.Context(1.0, 0.01, 1e-3)
     ctx.autotune(n)
+    assert ctx.get_run_path(n)["tuned"]
     x, v, m = _t(s.x), _t(s.v), _t(s.m)
     ctx.run(x, v, m, 10)
     ctx.sync()
