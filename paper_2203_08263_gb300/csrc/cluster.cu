@@ -12,7 +12,10 @@
 // first load and the final store (checkpoints aside), and no kernel boundary
 // separates the steps: at N of a few thousand the graph path's per-step
 // launch, bulk-copy and split-reduction latencies dominate, and this path
-// removes them.
+// removes them. Its grid form (N <= 8192) spreads the slices over a
+// cooperative grid of up to one CTA per SM instead of one cluster's 16: the
+// records go through a global double buffer and a bounded grid barrier, and
+// each CTA reloads all of them from L2 every step.
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -357,9 +360,6 @@ constexpr int kClusterThreads = 512;
 
 }  // namespace
 
-// Largest cluster this device can run the kernel with for n bodies (16 if
-// non-portable clusters are allowed and fit, else 8), 0 if none: the two
-// replicas must fit in shared memory.
 using ClusterFn = void (*)(const ClusterArgs);
 
 ClusterFn cluster_fn(bool f64, bool grid) {
@@ -370,9 +370,13 @@ ClusterFn cluster_fn(bool f64, bool grid) {
                : cluster_run_kernel<kClusterThreads, false, false>;
 }
 
+// Largest cluster this device can run the kernel with for n bodies (16 if
+// non-portable clusters are allowed and fit, else 8), 0 if none: the two
+// replicas must fit in shared memory.
 int cluster_run_size(int64_t n, bool f64) {
     if (n <= 0 || n > kClusterMaxN) return 0;
-    ClusterFn fn = cluster_fn(f64, false);    for (int c : {16, 8}) {
+    ClusterFn fn = cluster_fn(f64, false);
+    for (int c : {16, 8}) {
         const int64_t slice = ((n + c - 1) / c + 1) / 2 * 2;
         if (slice > kClusterThreads) continue;
         const size_t smem = (size_t)2 * c * slice * 16;
