@@ -110,7 +110,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     const bool f64 = f64_state(ctx);
     const bool fused = mode == 0 && (f64 || ctx->math == 0);
     const int cluster = fused && n <= kClusterMaxN ? cluster_run_size(n, f64) : 0;
-    const int grid = fused ? grid_run_ctas(n, ctx->num_sms) : 0;
+    const int grid = fused ? grid_run_ctas(n, ctx->num_sms, 8) : 0;
     if (cluster || grid) {
         void *x = ctx->tune[1].p, *v = ctx->tune[4].p, *m = ctx->tune[3].p;
         NB_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 3 * esize(ctx), st));
@@ -118,11 +118,30 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
         NB_CUDA(cudaMemsetAsync(m, 0, (size_t)n * esize(ctx), st));
         const int steps = 20;
         const int saved_path = ctx->run_path;
-        float ms_path[3] = {1e30f, 1e30f, 1e30f};
+        const std::string run_key = tune_key(ctx, mode, n) + "|run";
+        // candidates: graph, one cluster, and the grid form at slices of at
+        // least 8, 16 and 32 bodies (distinct CTA counts only); the grid form
+        // runs with the CTA count of a provisional "|run" entry
+        struct Cand { int path, size; };
+        std::vector<Cand> cands = {{1, 0}};
+        if (cluster) cands.push_back({2, cluster});
+        for (int ms : {8, 16, 32}) {
+            const int g = grid_run_ctas(n, ctx->num_sms, ms);
+            bool seen = false;
+            for (const Cand &c : cands) seen = seen || (c.path == 3 && c.size == g);
+            if (g && !seen) cands.push_back({3, g});
+        }
+        const auto saved_entry = ctx->tuned.find(run_key);
+        const bool had_entry = saved_entry != ctx->tuned.end();
+        const TuneEntry old_entry = had_entry ? saved_entry->second : TuneEntry{};
+        float best_ms = 1e30f;
+        Cand best_c = {1, 0};
         nb_status rs = NB_OK;
-        for (int path = 1; path <= 3 && rs == NB_OK; ++path) {
-            if ((path == 2 && !cluster) || (path == 3 && !grid)) continue;
-            ctx->run_path = path;
+        for (const Cand &cd : cands) {
+            if (rs != NB_OK) break;
+            ctx->run_path = cd.path == 3 ? 0 : cd.path;
+            if (cd.path == 3) ctx->tuned[run_key] = TuneEntry{2, cd.size, 0, 0, 0};
+            float ms = 1e30f;
             rs = run_device(ctx, n, x, v, m, steps, nullptr, 0, st);  // warm-up (and graph capture)
             for (int rep = 0; rs == NB_OK && rep < 3; ++rep) {
                 if (cudaEventRecord(e0, st) != cudaSuccess) { rs = NB_ERR_CUDA; break; }
@@ -133,17 +152,20 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
                 }
                 float t = 0;
                 cudaEventElapsedTime(&t, e0, e1);
-                ms_path[path - 1] = std::min(ms_path[path - 1], t);
+                ms = std::min(ms, t);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_c = cd;
             }
         }
         ctx->run_path = saved_path;
+        if (had_entry) ctx->tuned[run_key] = old_entry;
+        else ctx->tuned.erase(run_key);
         NB_TRY(rs);
         NB_TRY(sync_and_check(ctx, st));
-        int best_path = 0;  // 0 graph, 1 one cluster, 2 grid
-        for (int k = 1; k < 3; ++k)
-            if (ms_path[k] < ms_path[best_path]) best_path = k;
-        ctx->tuned[tune_key(ctx, mode, n) + "|run"] =
-            TuneEntry{best_path, best_path == 1 ? cluster : (best_path == 2 ? grid : 0), 0, 0, 0};
+        // stored: 0 graph, 1 one cluster, 2 grid; the cluster size or the grid's CTAs
+        ctx->tuned[run_key] = TuneEntry{best_c.path - 1, best_c.size, 0, 0, 0};
         clear_graphs(ctx);
     }
     save_tune_file(ctx);

@@ -452,13 +452,20 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
     return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
-// Grid form: CTAs for n bodies (slices of 2 * ceil(n / 32 / 2) bodies and
-// at most one CTA per SM), 0 if the path cannot run n bodies here.
-int grid_run_ctas(int64_t n, int num_sms) {
-    if (n <= 0 || n > kGridMaxN) return 0;
-    int64_t slice = std::max<int64_t>(16, ((n + num_sms - 1) / num_sms + 1) / 2 * 2);
+// Grid form: CTAs for n bodies with slices of at least min_slice bodies (even)
+// and at most one CTA per SM, 0 if the path cannot run n bodies here.
+int grid_run_ctas(int64_t n, int num_sms, int min_slice) {
+    if (n <= 0 || n > kGridMaxN || num_sms <= 0) return 0;
+    int64_t slice = std::max<int64_t>(min_slice, ((n + num_sms - 1) / num_sms + 1) / 2 * 2);
+    slice = (slice + 1) / 2 * 2;
     if (slice > kClusterThreads) return 0;
     return (int)((n + slice - 1) / slice);
+}
+
+bool grid_run_ctas_valid(int64_t n, int num_sms, int ctas) {
+    if (n <= 0 || n > kGridMaxN || ctas <= 0 || ctas > num_sms) return false;
+    const int64_t slice = ((n + ctas - 1) / ctas + 1) / 2 * 2;
+    return slice <= kClusterThreads;
 }
 
 cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, const void *m, int steps,

@@ -350,9 +350,13 @@ nb_status choose_run_path(nb_ctx *ctx, int64_t n, int *path, int *size) {
     }
     auto t = ctx->tuned.find(tune_key(ctx, 0, n) + "|run");
     if (t != ctx->tuned.end()) {
-        // tuned: 0 graph, 1 one cluster, 2 grid (a choice this device cannot run falls back)
+        // tuned: 0 graph, 1 one cluster, 2 grid with the tuned CTA count (a
+        // choice this device cannot run falls back to the graph path)
         if (t->second.pol == 1 && c) { *path = 2; *size = c; }
-        if (t->second.pol == 2 && g) { *path = 3; *size = g; }
+        if (t->second.pol == 2 && g) {
+            *path = 3;
+            *size = grid_run_ctas_valid(n, ctx->num_sms, t->second.nt) ? t->second.nt : g;
+        }
         return NB_OK;
     }
     if (c && n <= (f64 ? kClusterDefaultN64 : kClusterDefaultN)) {

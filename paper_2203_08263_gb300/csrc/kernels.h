@@ -98,7 +98,11 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
 constexpr int64_t kGridMaxN = 8192;  // one replica of 128 KiB
 constexpr int64_t kGridDefaultN = 4096;
 constexpr int64_t kGridDefaultN64 = 8192;
-int grid_run_ctas(int64_t n, int num_sms);
+// CTAs for n bodies with slices of at least min_slice bodies (16 untuned;
+// the tuner also tries 8 and 32), 0 if the path cannot run n bodies here;
+// and whether a tuned CTA count is runnable on this device.
+int grid_run_ctas(int64_t n, int num_sms, int min_slice = 16);
+bool grid_run_ctas_valid(int64_t n, int num_sms, int ctas);
 cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, const void *m, int steps,
                             int kdk, float eps2, double G, double dt, void *ckpt, int ckpt_every,
                             float4 *xm0, float4 *xm1, unsigned *bar, int *err, uint64_t timeout_ns,
