@@ -140,7 +140,8 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * graph). System s owns bodies [offsets[s], offsets[s+1]); offsets (int64,
  * nsys+1 entries, offsets[0] = 0, non-decreasing) may be a host or a device
  * pointer. Systems do not interact. Each system's size must be at most
- * nb_batched_max_n(); steps at most 2^20 per call. FP32 precision only.
+ * nb_batched_max_n(); steps at most 2^20 per call. FP32 precision only;
+ * either update scheme (params.scheme), as nb_run.
  * Inside the launch, work items (system, step, chunk of T x R i-bodies for
  * T threads per CTA; R = 8, 4, 2 or 1 per item: full chunks at the shape's
  * largest R, a system's ragged rest in smaller ones) are taken from one

@@ -23,8 +23,6 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     if (nsys < 0 || steps < 0) return fail(ctx, NB_ERR_INVALID, "nsys < 0 or steps < 0");
     if (nsys == 0 || steps == 0) return NB_OK;
     if (f64_state(ctx)) return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs are FP32 only");
-    if (ctx->p.scheme != NB_SCHEME_PAPER)
-        return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs use the paper scheme");
     if (!offsets) return fail(ctx, NB_ERR_INVALID, "offsets is NULL");
     NB_CUDA(cudaSetDevice(ctx->device));
     std::vector<int64_t> off;
@@ -49,14 +47,15 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
     NB_CUDA(batched_upload(plan, ctx->bat.p, st));
     char key[512];
-    snprintf(key, sizeof key, "bat|%d|%p|%p|%p|%d|%lld|%llx|%llu|%a|%a|%a", nsys, x, v, m, steps,
-             (long long)total, (unsigned long long)plan.signature,
+    const int kdk = ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0;
+    snprintf(key, sizeof key, "bat|%d|%p|%p|%p|%d|%d|%lld|%llx|%llu|%a|%a|%a", nsys, x, v, m, steps,
+             kdk, (long long)total, (unsigned long long)plan.signature,
              (unsigned long long)ctx->timeout_ns, ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = batched_enqueue(plan, ctx->bat.p, (float *)x, (float *)v, (const float *)m,
-                                         steps, (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
+                                         steps, kdk, (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
                                          (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, ctx->side);
         cudaGraph_t graph = nullptr;
         cudaError_t ce2 = cudaStreamEndCapture(ctx->side, &graph);
@@ -110,10 +109,10 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
             float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
             NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
             const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
-            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, eps2, (float)ctx->p.G,
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, 0, eps2, (float)ctx->p.G,
                                     (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
             NB_CUDA(cudaEventRecord(e0, st));
-            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, eps2, (float)ctx->p.G,
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, 0, eps2, (float)ctx->p.G,
                                     (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
             NB_CUDA(cudaEventRecord(e1, st));
             NB_CUDA(cudaEventSynchronize(e1));

@@ -33,6 +33,7 @@ struct BatchArgs {
     float4 *xm0, *xm1;
     float *x, *v;
     int steps, jt, items_per_step;
+    int kdk;  // 1: kick-drift-kick (kick twice between drifts; one closing half-kick step)
     float eps2, G, dt;
     int *err;
     uint64_t timeout_ns;
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
     const int f4_per_tile = a.jt;  // (jt / 2) records x 2 float4
     const uint32_t tile_bytes = (uint32_t)f4_per_tile * 16u;
     const float dt = a.dt;
-    const unsigned total = (unsigned)a.items_per_step * (unsigned)a.steps;
+    // KDK adds one step of items that only kick (the forces at the final positions)
+    const unsigned total = (unsigned)a.items_per_step * (unsigned)(a.steps + (a.kdk && a.steps > 0 ? 1 : 0));
 
     if (tid == 0) {
         for (int s = 0; s < kBS; ++s) {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
     // v), and the repacked position written to the other buffer. A generic
     // lambda, instantiated for each R the kernel holds.
     auto run_item = [&](auto r_const, const float4 *src, float4 *dst, int64_t b0, int64_t lo,
-                        int64_t hi, int ntl, int last_pairs) {
+                        int64_t hi, int ntl, int last_pairs, int t) {
         constexpr int R = decltype(r_const)::value;
         AccelF32x2::I ist[R];
         AccelF32x2::T tot[R];
@@ -255,6 +257,8 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
             }
         }
         kk += ntl;
+        const bool last_kick = a.kdk && t == a.steps;             // the closing half kick
+        const bool double_kick = a.kdk && t > 0 && !last_kick;    // KDK between two drifts
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t i = lo + r * NT + tid;
@@ -266,12 +270,16 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
                 float xs[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
-                    const float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                    // v += a dt/2 (the printed half kick; twice between two drifts of KDK); x += v dt
+                    float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                    if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
                     vp[cc] = vc;
-                    xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
-                    xp[cc] = xs[cc];
+                    if (!last_kick) {
+                        xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
+                        xp[cc] = xs[cc];
+                    }
                 }
-                pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
+                if (!last_kick) pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
             }
         }
     };
@@ -312,15 +320,15 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
         float4 *dst = ((t & 1) ? a.xm0 : a.xm1) + p0;
         if (!s_abort && !give_up) {
             if constexpr (RMAX >= 8) {
-                if (r == 8) run_item(std::integral_constant<int, 8>{}, src, dst, b0, lo, hi, ntl, last_pairs);
+                if (r == 8) run_item(std::integral_constant<int, 8>{}, src, dst, b0, lo, hi, ntl, last_pairs, t);
             }
             if constexpr (RMAX >= 4) {
-                if (r == 4) run_item(std::integral_constant<int, 4>{}, src, dst, b0, lo, hi, ntl, last_pairs);
+                if (r == 4) run_item(std::integral_constant<int, 4>{}, src, dst, b0, lo, hi, ntl, last_pairs, t);
             }
             if constexpr (RMAX >= 2) {
-                if (r == 2) run_item(std::integral_constant<int, 2>{}, src, dst, b0, lo, hi, ntl, last_pairs);
+                if (r == 2) run_item(std::integral_constant<int, 2>{}, src, dst, b0, lo, hi, ntl, last_pairs, t);
             }
-            if (r == 1) run_item(std::integral_constant<int, 1>{}, src, dst, b0, lo, hi, ntl, last_pairs);
+            if (r == 1) run_item(std::integral_constant<int, 1>{}, src, dst, b0, lo, hi, ntl, last_pairs, t);
             fence_proxy_async_global();
         }
         __syncthreads();
@@ -540,9 +548,9 @@ cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, float *x, 
 }
 
 cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *v, const float *m,
-                            int steps, float eps2, float G, float dt, int *err,
+                            int steps, int kdk, float eps2, float G, float dt, int *err,
                             uint64_t timeout_ns, cudaStream_t st) {
-    if ((uint64_t)p.items_per_step * (uint64_t)steps + (uint64_t)p.ncta >= (1ull << 32))
+    if ((uint64_t)p.items_per_step * (uint64_t)(steps + 1) + (uint64_t)p.ncta * (kHold + 1) >= (1ull << 32))
         return cudaErrorInvalidValue;
     Layout L = layout_of(p);
     char *b = (char *)scratch;
@@ -560,6 +568,7 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     a.x = x;
     a.v = v;
     a.steps = steps;
+    a.kdk = kdk;
     a.jt = p.jt;
     a.items_per_step = p.items_per_step;
     a.eps2 = eps2;

@@ -46,9 +46,10 @@ cudaError_t batched_upload(const BatchPlan &plan, void *scratch, cudaStream_t st
 cudaError_t batched_fill_synthetic(const BatchPlan &plan, void *scratch, float *x, float *v,
                                    float *m, cudaStream_t st);
 // Zero the queue and completion counters, pack every system, launch the
-// persistent kernel for `steps` paper steps.
+// persistent kernel for `steps` steps of the paper scheme (kdk = 0) or of
+// kick-drift-kick (kdk = 1).
 cudaError_t batched_enqueue(const BatchPlan &plan, void *scratch, float *x, float *v,
-                            const float *m, int steps, float eps2, float G, float dt, int *err,
-                            uint64_t timeout_ns, cudaStream_t st);
+                            const float *m, int steps, int kdk, float eps2, float G, float dt,
+                            int *err, uint64_t timeout_ns, cudaStream_t st);
 
 }  // namespace nb

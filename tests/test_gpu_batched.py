@@ -139,3 +139,20 @@ def test_set_batched_config_rejects_bad_shapes(nbm):
                       (512, 4, 64), (64, 1, 64), (0, 0, 64)):
         with pytest.raises(RuntimeError):
             ctx.set_batched_config(offt, nt, r, jt)
+
+
+def test_batched_kdk_every_system(nbm):
+    """Kick-drift-kick in the ensemble: each system against the oracle's KDK run."""
+    off, x, v, m = ics.ensemble(nsys=24, seed=41, nmin=64, nmax=3000)
+    ctx = nbm.Context(0.9, 0.02, 2e-3, scheme="kdk")
+    xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float32, device=DEV)
+    ctx.run_batched(torch.tensor(off, dtype=torch.int64), xt, vt, mt, 6)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s in range(24):
+        a, b = off[s], off[s + 1]
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 0.9, 0.02, 2e-3, 6, scheme="kdk")
+        assert rel_l2(gx[a:b], xr) <= 1e-5, s
+        assert rel_l2(gv[a:b], vr) <= 1e-4, s
