@@ -140,8 +140,9 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * graph). System s owns bodies [offsets[s], offsets[s+1]); offsets (int64,
  * nsys+1 entries, offsets[0] = 0, non-decreasing) may be a host or a device
  * pointer. Systems do not interact. Each system's size must be at most
- * nb_batched_max_n(); steps at most 2^20 per call. FP32 precision only;
- * either update scheme (params.scheme), as nb_run.
+ * nb_batched_max_n(); steps at most 2^20 per call. Either precision and
+ * either update scheme (params.precision, params.scheme), as nb_run; the
+ * precision form runs items of at most 4 bodies per thread.
  * Inside the launch, work items (system, step, chunk of T x R i-bodies for
  * T threads per CTA; R = 8, 4, 2 or 1 per item: full chunks at the shape's
  * largest R, a system's ragged rest in smaller ones) are taken from one
@@ -171,8 +172,9 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
  * Pin the batched launch shape for this size profile (offsets as for
  * nb_run_batched): threads per CTA and the largest R of an item, one of
  * 128 or 256 x {1, 2, 4, 8} or 512 x {1, 2}, and jtile, the j-bodies per
- * streamed tile (32, 64, 128 or 256). All three 0 removes a pinned or tuned
- * shape (back to the default). NB_ERR_INVALID for other values. Replaces
+ * streamed tile (32, 64, 128 or 256); the precision form takes R <= 4. All
+ * three 0 removes a pinned or tuned shape (back to the default).
+ * NB_ERR_INVALID for other values. Replaces
  * what nb_autotune_batched chose for these sizes. A tuning interface of this
  * library; the paper has no counterpart.
  */

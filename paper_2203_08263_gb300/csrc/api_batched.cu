@@ -22,7 +22,6 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     if (!ctx) return NB_ERR_INVALID;
     if (nsys < 0 || steps < 0) return fail(ctx, NB_ERR_INVALID, "nsys < 0 or steps < 0");
     if (nsys == 0 || steps == 0) return NB_OK;
-    if (f64_state(ctx)) return fail(ctx, NB_ERR_UNSUPPORTED, "batched runs are FP32 only");
     if (!offsets) return fail(ctx, NB_ERR_INVALID, "offsets is NULL");
     NB_CUDA(cudaSetDevice(ctx->device));
     std::vector<int64_t> off;
@@ -30,11 +29,13 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     const int64_t total = off[nsys];
     if (total == 0) return NB_OK;
     if (steps > (1 << 20)) return fail(ctx, NB_ERR_INVALID, "at most 2^20 steps per batched call");
-    NB_TRY(check_ptr(ctx, x, 4, "x", nullptr));
-    NB_TRY(check_ptr(ctx, v, 4, "v", nullptr));
-    NB_TRY(check_ptr(ctx, m, 4, "m", nullptr));
+    const size_t es = esize(ctx);
+    NB_TRY(check_ptr(ctx, x, es, "x", nullptr));
+    NB_TRY(check_ptr(ctx, v, es, "v", nullptr));
+    NB_TRY(check_ptr(ctx, m, es, "m", nullptr));
     cudaStream_t st = as_stream(stream);
     BatchPlan plan;
+    plan.f64 = f64_state(ctx) ? 1 : 0;
     auto tuned = ctx->batched_tuned.find(sizes_signature(off));
     if (tuned != ctx->batched_tuned.end()) {
         plan.nt = tuned->second.nt;
@@ -54,9 +55,9 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = batched_enqueue(plan, ctx->bat.p, (float *)x, (float *)v, (const float *)m,
-                                         steps, kdk, (float)(ctx->p.eps * ctx->p.eps), (float)ctx->p.G,
-                                         (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, ctx->side);
+        cudaError_t ce = batched_enqueue(plan, ctx->bat.p, x, v, m, steps, kdk,
+                                         (float)(ctx->p.eps * ctx->p.eps), ctx->p.G, ctx->p.dt,
+                                         ctx->err_word, ctx->timeout_ns, ctx->side);
         cudaGraph_t graph = nullptr;
         cudaError_t ce2 = cudaStreamEndCapture(ctx->side, &graph);
         if (ce != cudaSuccess || ce2 != cudaSuccess) {
@@ -84,9 +85,10 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
     const int64_t total = off[nsys];
     if (total == 0) return NB_OK;
-    NB_TRY(ensure(ctx, ctx->tune[1], (size_t)total * 12));
-    NB_TRY(ensure(ctx, ctx->tune[2], (size_t)total * 12));
-    NB_TRY(ensure(ctx, ctx->tune[3], (size_t)total * 4));
+    const size_t es = esize(ctx);
+    NB_TRY(ensure(ctx, ctx->tune[1], (size_t)total * 3 * es));
+    NB_TRY(ensure(ctx, ctx->tune[2], (size_t)total * 3 * es));
+    NB_TRY(ensure(ctx, ctx->tune[3], (size_t)total * es));
     cudaStream_t st = ctx->side;
     EventPair ev;
     NB_CUDA(ev.create());
@@ -98,7 +100,9 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
                                      {256, 2}, {256, 4}, {256, 8}, {512, 1}, {512, 2}};
     for (const auto &shape : kShapes) {
         for (int jt : {64, 128}) {
+            if (f64_state(ctx) && shape[1] > 4) continue;  // the precision form: R <= 4
             BatchPlan plan;
+            plan.f64 = f64_state(ctx) ? 1 : 0;
             plan.nt = shape[0];
             plan.r = shape[1];
             plan.jt = jt;
@@ -106,14 +110,14 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
             if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
             NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
             NB_CUDA(batched_upload(plan, ctx->bat.p, st));
-            float *x = (float *)ctx->tune[1].p, *v = (float *)ctx->tune[2].p, *m = (float *)ctx->tune[3].p;
+            void *x = ctx->tune[1].p, *v = ctx->tune[2].p, *m = ctx->tune[3].p;
             NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
             const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
-            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, 0, eps2, (float)ctx->p.G,
-                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, 0, eps2, ctx->p.G,
+                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
             NB_CUDA(cudaEventRecord(e0, st));
-            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, 0, eps2, (float)ctx->p.G,
-                                    (float)ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+            NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, 0, eps2, ctx->p.G,
+                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
             NB_CUDA(cudaEventRecord(e1, st));
             NB_CUDA(cudaEventSynchronize(e1));
             ctx->launches += 6;
@@ -140,6 +144,7 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     std::vector<int64_t> off;
     NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
     BatchPlan plan;
+    plan.f64 = f64_state(ctx) ? 1 : 0;
     auto tuned = ctx->batched_tuned.find(sizes_signature(off));
     if (tuned != ctx->batched_tuned.end()) {
         plan.nt = tuned->second.nt;
@@ -181,7 +186,10 @@ nb_status nb_set_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
                     "threads x bodies_per_thread must be 128 or 256 x {1,2,4,8}, or 512 x {1,2}");
     if (jtile != 32 && jtile != 64 && jtile != 128 && jtile != 256)
         return fail(ctx, NB_ERR_INVALID, "jtile must be 32, 64, 128 or 256");
+    if (f64_state(ctx) && bodies_per_thread > 4)
+        return fail(ctx, NB_ERR_INVALID, "the precision form takes at most 4 bodies per thread");
     BatchPlan plan;
+    plan.f64 = f64_state(ctx) ? 1 : 0;
     plan.nt = threads;
     plan.r = bodies_per_thread;
     plan.jt = jtile;

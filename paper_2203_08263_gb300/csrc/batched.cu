@@ -31,10 +31,11 @@ struct BatchArgs {
     unsigned *next;  // queue head
     unsigned *done;  // [nsys] items completed, cumulative over steps
     float4 *xm0, *xm1;
-    float *x, *v;
+    void *x, *v;  // [n][3] in the state type (float, or double in the precision form)
     int steps, jt, items_per_step;
     int kdk;  // 1: kick-drift-kick (kick twice between drifts; one closing half-kick step)
     float eps2, G, dt;
+    double Gd, dtd;  // the precision form's FP64 update
     int *err;
     uint64_t timeout_ns;
 };
@@ -85,7 +86,10 @@ constexpr int batched_min_blocks() {
     return per_sm / NT > 1 ? per_sm / NT : 1;
 }
 
-template <int NT, int RMAX>
+// F64 = true: the precision form, FP64 state; FP32 pair terms summed per
+// j-tile, two-summed into (hi, lo) across tiles, widened once for the FP64
+// update (the arithmetic of the single-system precision form).
+template <int NT, int RMAX, bool F64>
 __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_kernel(const BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
@@ -212,7 +216,14 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
                         int64_t hi, int ntl, int last_pairs, int t) {
         constexpr int R = decltype(r_const)::value;
         AccelF32x2::I ist[R];
-        AccelF32x2::T tot[R];
+        AccelF32x2::T tot[R];  // FP32: the sums; precision form: this tile's sums
+        float hh[F64 ? R : 1][3], ll[F64 ? R : 1][3];  // precision form: (hi, lo) across tiles
+        if constexpr (F64) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hh[r][c] = ll[r][c] = 0.f;
+        }
         AccelF32x2::C cst;
         cst.eps2 = dup(a.eps2);
 #pragma unroll
@@ -243,6 +254,21 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
 #pragma unroll
                     for (int r = 0; r < R; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
                 }
+                if constexpr (F64) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float b3[3] = {tot[r].x.x + tot[r].x.y, tot[r].y.x + tot[r].y.y,
+                                             tot[r].z.x + tot[r].z.y};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float sum, err;
+                            two_sum(hh[r][c], b3[c], sum, err);
+                            hh[r][c] = sum;
+                            ll[r][c] += err;
+                        }
+                        AccelF32x2::zero_total(tot[r]);
+                    }
+                }
                 __syncwarp();
                 if (lane == 0) {
                     // release the slot; the last warp refills it with position pos + kBS
@@ -263,23 +289,42 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
         for (int r = 0; r < R; ++r) {
             const int64_t i = lo + r * NT + tid;
             if (i < hi) {
-                const float acc[3] = {a.G * (tot[r].x.x + tot[r].x.y), a.G * (tot[r].y.x + tot[r].y.y),
-                                      a.G * (tot[r].z.x + tot[r].z.y)};
-                float *xp = a.x + 3 * (b0 + i);
-                float *vp = a.v + 3 * (b0 + i);
-                float xs[3];
+                if constexpr (!F64) {
+                    const float acc[3] = {a.G * (tot[r].x.x + tot[r].x.y), a.G * (tot[r].y.x + tot[r].y.y),
+                                          a.G * (tot[r].z.x + tot[r].z.y)};
+                    float *xp = reinterpret_cast<float *>(a.x) + 3 * (b0 + i);
+                    float *vp = reinterpret_cast<float *>(a.v) + 3 * (b0 + i);
+                    float xs[3];
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    // v += a dt/2 (the printed half kick; twice between two drifts of KDK); x += v dt
-                    float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
-                    if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
-                    vp[cc] = vc;
-                    if (!last_kick) {
-                        xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
-                        xp[cc] = xs[cc];
+                    for (int cc = 0; cc < 3; ++cc) {
+                        // v += a dt/2 (the printed half kick; twice between two drifts of KDK); x += v dt
+                        float vc = __fadd_rn(__ldcg(vp + cc), __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                        if (double_kick) vc = __fadd_rn(vc, __fmul_rn(__fmul_rn(acc[cc], dt), 0.5f));
+                        vp[cc] = vc;
+                        if (!last_kick) {
+                            xs[cc] = __fadd_rn(__ldcg(xp + cc), __fmul_rn(vc, dt));
+                            xp[cc] = xs[cc];
+                        }
                     }
+                    if (!last_kick) pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
+                } else {
+                    double *xp = reinterpret_cast<double *>(a.x) + 3 * (b0 + i);
+                    double *vp = reinterpret_cast<double *>(a.v) + 3 * (b0 + i);
+                    double xs[3];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const double acc = a.Gd * ((double)hh[r][cc] + (double)ll[r][cc]);
+                        double vc = __dadd_rn(__ldcg(vp + cc), __dmul_rn(__dmul_rn(acc, a.dtd), 0.5));
+                        if (double_kick) vc = __dadd_rn(vc, __dmul_rn(__dmul_rn(acc, a.dtd), 0.5));
+                        vp[cc] = vc;
+                        if (!last_kick) {
+                            xs[cc] = __dadd_rn(__ldcg(xp + cc), __dmul_rn(vc, a.dtd));
+                            xp[cc] = xs[cc];
+                        }
+                    }
+                    if (!last_kick)
+                        pair_put(dst, i, (float)xs[0], (float)xs[1], (float)xs[2], pair_get_cg(src, i, 3));
                 }
-                if (!last_kick) pair_put(dst, i, xs[0], xs[1], xs[2], pair_get_cg(src, i, 3));
             }
         }
     };
@@ -348,21 +393,23 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
     }
 }
 
+template <class TS>
 __global__ void batched_pack_kernel(const int64_t *off, const int64_t *poff, int jt,
-                                    const float *x, const float *m, float4 *xm) {
+                                    const TS *x, const TS *m, float4 *xm) {
     const int s = blockIdx.x;
     const int64_t b0 = off[s], n = off[s + 1] - b0, p0 = poff[s];
     const int64_t npad = (n + jt - 1) / jt * jt;
     for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) {
         if (i < n)
-            pair_put(xm + p0, i, x[3 * (b0 + i)], x[3 * (b0 + i) + 1], x[3 * (b0 + i) + 2],
-                     m[b0 + i]);
+            pair_put(xm + p0, i, (float)x[3 * (b0 + i)], (float)x[3 * (b0 + i) + 1],
+                     (float)x[3 * (b0 + i) + 2], (float)m[b0 + i]);
         else
             pair_put(xm + p0, i, 0.f, 0.f, 0.f, 0.f);
     }
 }
 
-__global__ void batched_fill_kernel(const int64_t *off, float *x, float *v, float *m) {
+template <class TS>
+__global__ void batched_fill_kernel(const int64_t *off, TS *x, TS *v, TS *m) {
     const int s = blockIdx.x;
     const int64_t b0 = off[s], n = off[s + 1] - b0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -373,10 +420,10 @@ __global__ void batched_fill_kernel(const int64_t *off, float *x, float *v, floa
             h *= 0x2c1b3c6dU;
             h ^= h >> 12;
             const float u = (float)(h >> 8) * (1.0f / 16777216.0f);
-            x[3 * g + c] = 2.f * u - 1.f;
-            v[3 * g + c] = 0.1f * (u - 0.5f);
+            x[3 * g + c] = (TS)(2.f * u - 1.f);
+            v[3 * g + c] = (TS)(0.1f * (u - 0.5f));
         }
-        m[g] = 1.0f / (float)n;
+        m[g] = (TS)(1.0f / (float)n);
     }
 }
 
@@ -387,18 +434,31 @@ using BatchedFn = void (*)(const BatchArgs);
 // Shapes of the ensemble kernel: (threads, largest R). Up to R = 2 the
 // registers fit 512 resident threads per SM; the 512-thread forms then run
 // one CTA per SM.
-BatchedFn batched_fn(int nt, int rmax) {
+BatchedFn batched_fn(int nt, int rmax, bool f64) {
+    if (f64) {  // (hi, lo) per body on top of the sums: at most 4 bodies per thread
+        switch (nt * 16 + rmax) {
+            case 128 * 16 + 1: return batched_kernel<128, 1, true>;
+            case 128 * 16 + 2: return batched_kernel<128, 2, true>;
+            case 128 * 16 + 4: return batched_kernel<128, 4, true>;
+            case 256 * 16 + 1: return batched_kernel<256, 1, true>;
+            case 256 * 16 + 2: return batched_kernel<256, 2, true>;
+            case 256 * 16 + 4: return batched_kernel<256, 4, true>;
+            case 512 * 16 + 1: return batched_kernel<512, 1, true>;
+            case 512 * 16 + 2: return batched_kernel<512, 2, true>;
+            default: return nullptr;
+        }
+    }
     switch (nt * 16 + rmax) {
-        case 128 * 16 + 1: return batched_kernel<128, 1>;
-        case 128 * 16 + 2: return batched_kernel<128, 2>;
-        case 128 * 16 + 4: return batched_kernel<128, 4>;
-        case 128 * 16 + 8: return batched_kernel<128, 8>;
-        case 256 * 16 + 1: return batched_kernel<256, 1>;
-        case 256 * 16 + 2: return batched_kernel<256, 2>;
-        case 256 * 16 + 4: return batched_kernel<256, 4>;
-        case 256 * 16 + 8: return batched_kernel<256, 8>;
-        case 512 * 16 + 1: return batched_kernel<512, 1>;
-        case 512 * 16 + 2: return batched_kernel<512, 2>;
+        case 128 * 16 + 1: return batched_kernel<128, 1, false>;
+        case 128 * 16 + 2: return batched_kernel<128, 2, false>;
+        case 128 * 16 + 4: return batched_kernel<128, 4, false>;
+        case 128 * 16 + 8: return batched_kernel<128, 8, false>;
+        case 256 * 16 + 1: return batched_kernel<256, 1, false>;
+        case 256 * 16 + 2: return batched_kernel<256, 2, false>;
+        case 256 * 16 + 4: return batched_kernel<256, 4, false>;
+        case 256 * 16 + 8: return batched_kernel<256, 8, false>;
+        case 512 * 16 + 1: return batched_kernel<512, 1, false>;
+        case 512 * 16 + 2: return batched_kernel<512, 2, false>;
         default: return nullptr;
     }
 }
@@ -439,9 +499,9 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
     (void)device;
     p.nsys = (int)off.size() - 1;
     if (p.nt == 0) p.nt = 256;  // one CTA per SM: no co-resident CTA starves another
-    if (p.r == 0) p.r = 8;
+    if (p.r == 0) p.r = p.f64 ? 4 : 8;
     if (p.jt == 0) p.jt = 64;
-    const BatchedFn fn = batched_fn(p.nt, p.r);
+    const BatchedFn fn = batched_fn(p.nt, p.r, p.f64 != 0);
     if (!fn || p.jt % 2 || kPadBodies % p.jt) {
         why = "unsupported batched shape";
         return false;
@@ -539,16 +599,19 @@ cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
     return cudaSuccess;
 }
 
-cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, float *x, float *v,
-                                   float *m, cudaStream_t st) {
+cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, void *x, void *v, void *m,
+                                   cudaStream_t st) {
     Layout L = layout_of(p);
-    batched_fill_kernel<<<p.nsys, 256, 0, st>>>((const int64_t *)((char *)scratch + L.o_off), x, v,
-                                                m);
+    const int64_t *off = (const int64_t *)((char *)scratch + L.o_off);
+    if (p.f64)
+        batched_fill_kernel<double><<<p.nsys, 256, 0, st>>>(off, (double *)x, (double *)v, (double *)m);
+    else
+        batched_fill_kernel<float><<<p.nsys, 256, 0, st>>>(off, (float *)x, (float *)v, (float *)m);
     return cudaGetLastError();
 }
 
-cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *v, const float *m,
-                            int steps, int kdk, float eps2, float G, float dt, int *err,
+cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, void *x, void *v, const void *m,
+                            int steps, int kdk, float eps2, double G, double dt, int *err,
                             uint64_t timeout_ns, cudaStream_t st) {
     if ((uint64_t)p.items_per_step * (uint64_t)(steps + 1) + (uint64_t)p.ncta * (kHold + 1) >= (1ull << 32))
         return cudaErrorInvalidValue;
@@ -572,13 +635,20 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     a.jt = p.jt;
     a.items_per_step = p.items_per_step;
     a.eps2 = eps2;
-    a.G = G;
-    a.dt = dt;
+    a.G = (float)G;
+    a.dt = (float)dt;
+    a.Gd = G;
+    a.dtd = dt;
     a.err = err;
     a.timeout_ns = timeout_ns;
     cudaError_t e = cudaMemsetAsync(b + L.o_next, 0, L.o_xm0 - L.o_next, st);
     if (e != cudaSuccess) return e;
-    batched_pack_kernel<<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, x, m, a.xm0);
+    if (p.f64)
+        batched_pack_kernel<double><<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, (const double *)x,
+                                                            (const double *)m, a.xm0);
+    else
+        batched_pack_kernel<float><<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, (const float *)x,
+                                                           (const float *)m, a.xm0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -592,7 +662,7 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, float *x, float *
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BatchedFn fn = batched_fn(p.nt, p.r);
+    BatchedFn fn = batched_fn(p.nt, p.r, p.f64 != 0);
     if (!fn) return cudaErrorInvalidValue;
     return cudaLaunchKernelEx(&cfg, fn, a);
 }

@@ -19,10 +19,11 @@ namespace nb {
 // unfinished item can always run).
 struct BatchPlan {
     int nsys = 0;
-    int nt = 256, r = 8, jt = 64;   // kernel shape: threads, largest R, j-tile
+    int nt = 0, r = 0, jt = 0;      // kernel shape: threads, largest R, j-tile (0: the default)
     int ncta = 0;                   // persistent grid (resident CTAs)
     int items_per_step = 0;
     int origin = 0;                 // 0 default shape, 1 autotuned, 2 set by the caller
+    int f64 = 0;                    // the precision form (FP64 state): shapes up to R = 4
     int64_t total = 0, total_pad = 0;
     std::vector<int64_t> off, poff;  // body offsets, packed offsets (per system)
     std::vector<int> item_sys, item_lo, item_r;  // per item of one step
@@ -42,14 +43,15 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
 // Copy the plan's arrays into `scratch` on `st`.
 cudaError_t batched_upload(const BatchPlan &plan, void *scratch, cudaStream_t st);
 // Deterministic synthetic state for tuning runs (positions in [-1,1]^3,
-// small velocities, masses 1/N_s): timing does not depend on the values.
-cudaError_t batched_fill_synthetic(const BatchPlan &plan, void *scratch, float *x, float *v,
-                                   float *m, cudaStream_t st);
+// small velocities, masses 1/N_s; float or double per plan.f64): timing does
+// not depend on the values.
+cudaError_t batched_fill_synthetic(const BatchPlan &plan, void *scratch, void *x, void *v, void *m,
+                                   cudaStream_t st);
 // Zero the queue and completion counters, pack every system, launch the
 // persistent kernel for `steps` steps of the paper scheme (kdk = 0) or of
 // kick-drift-kick (kdk = 1).
-cudaError_t batched_enqueue(const BatchPlan &plan, void *scratch, float *x, float *v,
-                            const float *m, int steps, int kdk, float eps2, float G, float dt,
+cudaError_t batched_enqueue(const BatchPlan &plan, void *scratch, void *x, void *v,
+                            const void *m, int steps, int kdk, float eps2, double G, double dt,
                             int *err, uint64_t timeout_ns, cudaStream_t st);
 
 }  // namespace nb

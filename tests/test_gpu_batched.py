@@ -156,3 +156,49 @@ def test_batched_kdk_every_system(nbm):
         xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 0.9, 0.02, 2e-3, 6, scheme="kdk")
         assert rel_l2(gx[a:b], xr) <= 1e-5, s
         assert rel_l2(gv[a:b], vr) <= 1e-4, s
+
+
+@pytest.mark.parametrize("scheme", ["paper", "kdk"])
+def test_batched_precision_form_every_system(nbm, scheme):
+    """FP64 state with compensated FP32 forces in the ensemble: every system at
+    the tolerances of the single-system precision-form run (Plummer spheres)."""
+    sizes = [3, 200, 1000, 1500, 2100, 700]
+    parts = [ics.plummer(n, seed=60 + k) for k, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x = np.concatenate([p.x for p in parts])
+    v = np.concatenate([p.v for p in parts])
+    m = np.concatenate([p.m for p in parts])
+    ctx = nbm.Context(1.0, 0.05, 5e-4, precision="comp", scheme=scheme)
+    xt = torch.tensor(x, dtype=torch.float64, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float64, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float64, device=DEV)
+    offt = torch.tensor(off, dtype=torch.int64)
+    assert ctx.get_batched_config(offt)["bodies_per_thread"] <= 4
+    ctx.run_batched(offt, xt, vt, mt, 10)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s_ in range(len(sizes)):
+        a, b = off[s_], off[s_ + 1]
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.05, 5e-4, 10, scheme=scheme)
+        assert rel_l2(gx[a:b], xr) <= 1e-9, s_
+        assert rel_l2(gv[a:b], vr) <= 1e-6, s_
+
+
+def test_batched_precision_form_tuned_and_pinned(nbm):
+    off, x, v, m = ics.ensemble(nsys=30, seed=9, nmin=64, nmax=2048)
+    ctx = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
+    offt = torch.tensor(off, dtype=torch.int64)
+    with pytest.raises(RuntimeError):
+        ctx.set_batched_config(offt, 256, 8, 64)  # above 4 bodies per thread
+    ctx.autotune_batched(offt)
+    cfg = ctx.get_batched_config(offt)
+    assert cfg["tuned"] and cfg["bodies_per_thread"] <= 4
+    xt = torch.tensor(x, dtype=torch.float64, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float64, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float64, device=DEV)
+    ctx.run_batched(offt, xt, vt, mt, 4)
+    ctx.sync()
+    for s_ in (0, 11, 29):
+        a, b = off[s_], off[s_ + 1]
+        xr, _ = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 4)
+        assert rel_l2(to_np(xt)[a:b], xr) <= 1e-9
