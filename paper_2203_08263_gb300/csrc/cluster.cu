@@ -127,7 +127,10 @@ constexpr int kCompBlockPairs = 32;
 // per SM; each step every CTA writes its slice's records to a global buffer,
 // meets the others at a grid barrier and reloads all records into its shared
 // memory.
-template <int NT, bool F64, bool GRID>
+// RB = bodies per lane in the force sum (1, or 2 for slices of 64 or more:
+// each j-record then feeds four interactions instead of two, halving the
+// shared-memory traffic per interaction).
+template <int NT, bool F64, bool GRID, int RB>
 __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a) {
     using TS = typename std::conditional<F64, double, float>::type;
     extern __shared__ __align__(16) float4 rep[];  // cluster: [2][npad]; grid: [npad]
@@ -141,24 +144,34 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
     __shared__ int s_ok;
     const int S = a.slice;
     const int npad = a.npad;
-    // Thread mapping of the force sum: lane l of warp w sums body
-    // il = (w / Q) * 32 + l over the j-pairs jq, jq + Q, ... with jq = w % Q,
-    // so all lanes of a warp read the same j-record (a broadcast load: the
-    // j-split across lanes of one warp cost 8 shared-memory wavefronts per
-    // 16-byte load). The Q partial sums of a body meet in shared memory.
-    const int spad = (S + 31) / 32 * 32;  // body slots in whole warps
-    const int Q = NT / spad;              // j-splits per body (>= 1: slice <= NT)
+    // Thread mapping of the force sum: lane l of warp w sums the RB bodies in
+    // slots (w / Q) * 32 RB + r * 32 + l over the j-pairs jq, jq + Q, ... with
+    // jq = w % Q, so all lanes of a warp read the same j-record (a broadcast
+    // load: the j-split across lanes of one warp cost 8 shared-memory
+    // wavefronts per 16-byte load). The Q partial sums of a body meet in
+    // shared memory.
+    constexpr int kRow = 32 * RB;                    // body slots per warp row
+    const int spad = (S + kRow - 1) / kRow * kRow;   // body slots in whole rows
+    const int rows = spad / kRow;
+    const int Q = (NT / 32) / rows;                  // j-splits per body (>= 1)
     const int warp = tid >> 5, lane = tid & 31;
     const int jq = warp % Q;
-    const int il = (warp / Q) * 32 + lane;
-    const bool active = warp < Q * (spad / 32) && il < S;  // sums forces for body i
-    const int i = (int)rank * S + (active ? il : 0);
+    const bool in_row = warp < Q * rows;
+    int il[RB], i[RB];  // body slots of this lane, their global indices
+    bool act[RB];       // the slot holds a body of the slice
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        il[r] = (warp / Q) * kRow + r * 32 + lane;
+        act[r] = in_row && il[r] < S;
+        i[r] = (int)rank * S + (act[r] ? il[r] : 0);
+    }
+    const bool active = act[0];  // slot 0 of a lane is filled first
     // The thread that keeps body io's x and v and updates it: thread k of the
     // CTA for body k of the slice (the update's FP64 in the precision form is
     // slow on this part; compact owners fill ceil(S / 32) warps).
     const int io = (int)rank * S + tid;
     const bool owner = tid < S && io < a.n;
-    __shared__ float s_red[NT * (F64 ? 6 : 3)];  // per (split, body): partial sums (hi, lo)
+    __shared__ float s_red[NT * RB * (F64 ? 6 : 3)];  // per (split, body slot): partial sums (hi, lo)
     if constexpr (!GRID) {
         // both replicas: every body's record in buffer 0, zeros in buffer 1
         for (int k = tid; k < npad; k += NT) {
@@ -215,63 +228,86 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
             dst = rep + (cur ^ 1) * npad;
         }
         TS ax = 0, ay = 0, az = 0;
-        AccelF32x2::I ist;
+        AccelF32x2::I ist[RB];
         AccelF32x2::C cst;
         cst.eps2 = dup(a.eps2);
-        ist.nx = dup(-pair_get(src, i, 0));
-        ist.ny = dup(-pair_get(src, i, 1));
-        ist.nz = dup(-pair_get(src, i, 2));
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            ist[r].nx = dup(-pair_get(src, i[r], 0));
+            ist[r].ny = dup(-pair_get(src, i[r], 1));
+            ist[r].nz = dup(-pair_get(src, i[r], 2));
+        }
         const int npairs = npad >> 1;
         if constexpr (!F64) {
             if (active) {
-                AccelF32x2::T tot;
-                AccelF32x2::zero_total(tot);
+                AccelF32x2::T tot[RB];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) AccelF32x2::zero_total(tot[r]);
 #pragma unroll 4
                 for (int p = jq; p < npairs; p += Q) {
                     const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
-                    AccelF32x2::interact(rec, ist, tot, cst);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) AccelF32x2::interact(rec, ist[r], tot[r], cst);
                 }
-                float *r = s_red + 3 * (jq * spad + il);
-                r[0] = tot.x.x + tot.x.y;
-                r[1] = tot.y.x + tot.y.y;
-                r[2] = tot.z.x + tot.z.y;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    if (!act[r]) continue;
+                    float *rr = s_red + 3 * (jq * spad + il[r]);
+                    rr[0] = tot[r].x.x + tot[r].x.y;
+                    rr[1] = tot[r].y.x + tot[r].y.y;
+                    rr[2] = tot[r].z.x + tot[r].z.y;
+                }
             }
             __syncthreads();
             if (owner) {
                 for (int q = 0; q < Q; ++q) {  // the body's splits in order
-                    const float *r = s_red + 3 * (q * spad + tid);
-                    ax += r[0];
-                    ay += r[1];
-                    az += r[2];
+                    const float *rr = s_red + 3 * (q * spad + tid);
+                    ax += rr[0];
+                    ay += rr[1];
+                    az += rr[2];
                 }
             }
         } else {
             // blocks of FP32 partial sums two-summed into (hi, lo) per split ...
             if (active) {
-                float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+                float h[RB][3], l[RB][3];
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) h[r][c] = l[r][c] = 0.f;
                 for (int p0 = jq; p0 < npairs; p0 += Q * kCompBlockPairs) {
-                    AccelF32x2::T blk;
-                    AccelF32x2::zero_total(blk);
+                    AccelF32x2::T blk[RB];
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) AccelF32x2::zero_total(blk[r]);
                     const int pend = min(npairs, p0 + Q * kCompBlockPairs);
 #pragma unroll 4
                     for (int p = p0; p < pend; p += Q) {
                         const float4 rec[2] = {src[2 * p], src[2 * p + 1]};
-                        AccelF32x2::interact(rec, ist, blk, cst);
-                    }
-                    const float b3[3] = {blk.x.x + blk.x.y, blk.y.x + blk.y.y, blk.z.x + blk.z.y};
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        float sum, err;
-                        two_sum(h[c], b3[c], sum, err);
-                        h[c] = sum;
-                        l[c] += err;
+                        for (int r = 0; r < RB; ++r) AccelF32x2::interact(rec, ist[r], blk[r], cst);
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const float b3[3] = {blk[r].x.x + blk[r].x.y, blk[r].y.x + blk[r].y.y,
+                                             blk[r].z.x + blk[r].z.y};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float sum, err;
+                            two_sum(h[r][c], b3[c], sum, err);
+                            h[r][c] = sum;
+                            l[r][c] += err;
+                        }
                     }
                 }
-                float *r = s_red + 6 * (jq * spad + il);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    r[c] = h[c];
-                    r[3 + c] = l[c];
+                for (int r = 0; r < RB; ++r) {
+                    if (!act[r]) continue;
+                    float *rr = s_red + 6 * (jq * spad + il[r]);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        rr[c] = h[r][c];
+                        rr[3 + c] = l[r][c];
+                    }
                 }
             }
             __syncthreads();
@@ -279,13 +315,13 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
             if (owner) {
                 float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
                 for (int q = 0; q < Q; ++q) {
-                    const float *r = s_red + 6 * (q * spad + tid);
+                    const float *rr = s_red + 6 * (q * spad + tid);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         float sum, err;
-                        two_sum(h[c], r[c], sum, err);
+                        two_sum(h[c], rr[c], sum, err);
                         h[c] = sum;
-                        l[c] = __fadd_rn(l[c], __fadd_rn(r[3 + c], err));
+                        l[c] = __fadd_rn(l[c], __fadd_rn(rr[3 + c], err));
                     }
                 }
                 ax = (double)h[0] + (double)l[0];
@@ -362,23 +398,33 @@ constexpr int kClusterThreads = 512;
 
 using ClusterFn = void (*)(const ClusterArgs);
 
-ClusterFn cluster_fn(bool f64, bool grid) {
+ClusterFn cluster_fn(bool f64, bool grid, int rb) {
+    if (rb == 2) {
+        if (grid)
+            return f64 ? cluster_run_kernel<kClusterThreads, true, true, 2>
+                       : cluster_run_kernel<kClusterThreads, false, true, 2>;
+        return f64 ? cluster_run_kernel<kClusterThreads, true, false, 2>
+                   : cluster_run_kernel<kClusterThreads, false, false, 2>;
+    }
     if (grid)
-        return f64 ? cluster_run_kernel<kClusterThreads, true, true>
-                   : cluster_run_kernel<kClusterThreads, false, true>;
-    return f64 ? cluster_run_kernel<kClusterThreads, true, false>
-               : cluster_run_kernel<kClusterThreads, false, false>;
+        return f64 ? cluster_run_kernel<kClusterThreads, true, true, 1>
+                   : cluster_run_kernel<kClusterThreads, false, true, 1>;
+    return f64 ? cluster_run_kernel<kClusterThreads, true, false, 1>
+               : cluster_run_kernel<kClusterThreads, false, false, 1>;
 }
+
+// Bodies per lane for a slice: two once a warp row of 64 slots is mostly filled.
+int cluster_rb(int64_t slice) { return slice >= 64 ? 2 : 1; }
 
 // Largest cluster this device can run the kernel with for n bodies (16 if
 // non-portable clusters are allowed and fit, else 8), 0 if none: the two
 // replicas must fit in shared memory.
 int cluster_run_size(int64_t n, bool f64) {
     if (n <= 0 || n > kClusterMaxN) return 0;
-    ClusterFn fn = cluster_fn(f64, false);
     for (int c : {16, 8}) {
         const int64_t slice = ((n + c - 1) / c + 1) / 2 * 2;
         if (slice > kClusterThreads) continue;
+        ClusterFn fn = cluster_fn(f64, false, cluster_rb(slice));
         const size_t smem = (size_t)2 * c * slice * 16;
         if (smem > 200 * 1024) continue;
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -409,10 +455,10 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
                                int steps, int kdk, float eps2, double G, double dt, void *ckpt,
                                int ckpt_every, cudaStream_t st) {
     if (cluster <= 0 || n <= 0 || n > kClusterMaxN) return cudaErrorInvalidValue;
-    ClusterFn fn = cluster_fn(f64, false);
     ClusterArgs a;
     a.n = (int)n;
     a.slice = (int)(((n + cluster - 1) / cluster + 1) / 2 * 2);
+    ClusterFn fn = cluster_fn(f64, false, cluster_rb(a.slice));
     a.npad = cluster * a.slice;
     a.steps = steps;
     a.kdk = kdk;
@@ -473,11 +519,11 @@ cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, con
                             float4 *xm0, float4 *xm1, unsigned *bar, int *err, uint64_t timeout_ns,
                             int stall, cudaStream_t st) {
     if (ctas <= 0 || n <= 0 || n > kGridMaxN) return cudaErrorInvalidValue;
-    ClusterFn fn = cluster_fn(f64, true);
     ClusterArgs a;
     a.n = (int)n;
     a.slice = (int)(((n + ctas - 1) / ctas + 1) / 2 * 2);
     if (a.slice > kClusterThreads) return cudaErrorInvalidValue;
+    ClusterFn fn = cluster_fn(f64, true, cluster_rb(a.slice));
     a.npad = ctas * a.slice;
     a.steps = steps;
     a.kdk = kdk;
