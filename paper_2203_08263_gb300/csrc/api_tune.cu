@@ -120,12 +120,13 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
         const int saved_path = ctx->run_path;
         const std::string run_key = tune_key(ctx, mode, n) + "|run";
         // candidates: graph, one cluster, and the grid form at slices of at
-        // least 8, 16 and 32 bodies (distinct CTA counts only); the grid form
+        // least 8, 16, 32 and 64 bodies (distinct CTA counts only; 64 takes the
+        // two-bodies-per-lane form); the grid form
         // runs with the CTA count of a provisional "|run" entry
         struct Cand { int path, size; };
         std::vector<Cand> cands = {{1, 0}};
         if (cluster) cands.push_back({2, cluster});
-        for (int ms : {8, 16, 32}) {
+        for (int ms : {8, 16, 32, 64}) {
             const int g = grid_run_ctas(n, ctx->num_sms, ms);
             bool seen = false;
             for (const Cand &c : cands) seen = seen || (c.path == 3 && c.size == g);

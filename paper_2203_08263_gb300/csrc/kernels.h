@@ -99,7 +99,7 @@ constexpr int64_t kGridMaxN = 8192;  // one replica of 128 KiB
 constexpr int64_t kGridDefaultN = 4096;
 constexpr int64_t kGridDefaultN64 = 8192;
 // CTAs for n bodies with slices of at least min_slice bodies (16 untuned;
-// the tuner also tries 8 and 32), 0 if the path cannot run n bodies here;
+// the tuner also tries 8, 32 and 64), 0 if the path cannot run n bodies here;
 // and whether a tuned CTA count is runnable on this device.
 int grid_run_ctas(int64_t n, int num_sms, int min_slice = 16);
 bool grid_run_ctas_valid(int64_t n, int num_sms, int ctas);
