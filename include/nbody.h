@@ -109,6 +109,17 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  *   a[i][c] = G sum_j m_j (x_j - x_i)_c / (|x_j - x_i|^2 + eps^2)^(3/2).
  * x [n][3], m [n] in the state type; a [n][3] in the state type (float32 or
  * float64). Inputs are read-only.
+ *
+ * Force forms (the same sum in every form; nb_get_form tells which one
+ * serves a size): in FP32 a one-sided kernel sums over j for every i; from
+ * n = 32768 up (or where nb_autotune finds it faster) a pair-symmetric
+ * kernel evaluates each unordered pair {i, j} once and adds its term to both
+ * bodies with opposite signs (Newton's third law), into per-block partials
+ * that a second kernel adds in a fixed order. It keeps nb x 3 x npad floats
+ * of partials in the context (nb = npad / 1024 blocks of 1024 bodies,
+ * npad = n rounded up to a block: about 12 n^2 / 1024 bytes, 0.8 GB at
+ * n = 262144); systems whose partials would exceed 8 GiB use the one-sided
+ * kernel. Results are deterministic in every form.
  */
 nb_status nb_accel(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a,
                    void *stream);
@@ -231,6 +242,23 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode);
  * 1 if the shape came from a tuning run}. */
 nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5);
 
+/* Force-sum forms (nb_get_form). */
+typedef enum {
+    NB_FORM_F32X2 = 0,           /* FP32, one-sided, packed f32x2 arithmetic */
+    NB_FORM_SCALAR = 1,          /* FP32, one-sided, scalar arithmetic */
+    NB_FORM_COMPENSATED = 2,     /* compensated FP32, FP64 state */
+    NB_FORM_POTENTIAL = 3,       /* softened potential (nb_energy) */
+    NB_FORM_VJP = 4,             /* adjoint VJP, FP32 */
+    NB_FORM_VJP_COMPENSATED = 5, /* adjoint VJP, compensated, FP64 state */
+    NB_FORM_SQRT_DIV = 6,        /* ablation: sqrt then division */
+    NB_FORM_POW = 7,             /* ablation: powf */
+    NB_FORM_PAIR_SYMMETRIC = 8   /* FP32, each unordered pair once */
+} nb_form;
+
+/* The force-sum form (nb_form) the context would use for (n, mode), mode as
+ * in nb_get_config (2 = the potential of nb_energy). */
+nb_status nb_get_form(nb_ctx *ctx, int64_t n, int mode, int *form);
+
 /* The nb_run path the context would use for n bodies: out[0] = 1 graph of
  * force launches, 2 one-cluster kernel, 3 its grid form; out[1] = the
  * cluster size or the grid's CTAs (0 for the graph path); out[2] = 1 if the
@@ -266,7 +294,12 @@ typedef enum {
     /* nb_run path: 0 = chosen per size (default), 1 = graph of force
      * launches, 2 = one-cluster kernel, 3 = its grid form
      * (NB_ERR_UNSUPPORTED at nb_run when the system does not qualify). */
-    NB_DBG_RUN_PATH = 4
+    NB_DBG_RUN_PATH = 4,
+    /* FP32 forward force form: 0 = chosen per size (default), 1 = one-sided
+     * kernels only, 512 or 1024 = the pair-symmetric kernel with blocks of
+     * that many bodies at every size (nb_run's graph path; the fused
+     * small-system paths keep their own kernel). */
+    NB_DBG_FORM = 5
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 

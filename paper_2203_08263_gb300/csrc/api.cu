@@ -248,6 +248,13 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         ctx->run_path = (int)value;
         return NB_OK;
     }
+    if (key == NB_DBG_FORM) {
+        if (value != 0 && value != 1 && value != 512 && value != 1024)
+            return fail(ctx, NB_ERR_INVALID, "force form must be 0, 1, 512 or 1024");
+        ctx->form_pin = (int)value;
+        clear_graphs(ctx);
+        return NB_OK;
+    }
     if (key == NB_DBG_STALL_PRODUCER) {
         if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
         ctx->debug = value ? (ctx->debug | kDbgStallProducer) : (ctx->debug & ~kDbgStallProducer);

@@ -142,7 +142,12 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
                                                 ctx->adj_v[b].p, ctx->side2)))
                 return;
             ctx->launches += 1;
-            rs = pack(ctx, n, npad, ctx->adj_x[b].p, nullptr, m, traj_slot(b, 0), nullptr, ctx->side2);
+            PadTargets pads;  // the recomputed steps' records
+            pads.base = traj_slot(b, 1);
+            pads.count = k - 1;
+            pads.stride = traj_slot(b, 1) - traj_slot(b, 0);
+            rs = pack(ctx, n, npad, ctx->adj_x[b].p, nullptr, m, traj_slot(b, 0), nullptr, ctx->side2,
+                      pads);
             for (int t = 0; rs == NB_OK && t < k - 1; ++t) {
                 ForceArgs a = base_args(ctx, pf, n, traj_slot(b, t));
                 a.part = (float4 *)ctx->part2.p;

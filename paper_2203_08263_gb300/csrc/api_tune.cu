@@ -22,13 +22,15 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     std::vector<int> pols;
     if (mode == 0) {
         if (f64_state(ctx)) pols = {kPolComp};
+        else if (ctx->math == 0 && n >= 8192) pols = {kPolF32x2, kPolScalar, kPolSym};
         else pols = {kPolF32x2, kPolScalar};
     } else {
         pols = {f64_state(ctx) ? kPolVjpComp : kPolVjp};
     }
     const int64_t npad = round_up(n, kPadBodies);
     const size_t es = esize(ctx);
-    NB_TRY(ensure(ctx, ctx->tune[0], (size_t)npad * 40));          // records
+    // records, up to the pair-symmetric policy's padding to 1024 bodies
+    NB_TRY(ensure(ctx, ctx->tune[0], (size_t)round_up(n, 1024) * 40));
     NB_TRY(ensure(ctx, ctx->tune[1], (size_t)n * 3 * 8, true));    // out / xbar
     NB_TRY(ensure(ctx, ctx->tune[2], (size_t)n * 8, true));        // mbar
     NB_TRY(ensure(ctx, ctx->tune[3], (size_t)n * 8, true));        // mass
@@ -41,9 +43,10 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     auto time_shape = [&](const Shape &s, float *ms) -> nb_status {
         Plan p;
         NB_TRY(make_plan(ctx, s, n, &p));
-        if (p.part_bytes > ((size_t)1 << 31)) { *ms = 1e30f; return NB_OK; }
+        const size_t cap = s.pol == kPolSym ? kSymMaxPartBytes : ((size_t)1 << 31);
+        if (p.part_bytes > cap) { *ms = 1e30f; return NB_OK; }
         NB_TRY(plan_scratch(ctx, p));
-        NB_CUDA(launch_fill_synthetic(n, npad, (float4 *)ctx->tune[0].p, pol_rec_f4(s.pol), st));
+        NB_CUDA(launch_fill_synthetic(n, p.npad, (float4 *)ctx->tune[0].p, pol_rec_f4(s.pol), st));
         ForceArgs a = base_args(ctx, p, n, (const float4 *)ctx->tune[0].p);
         a.op = mode == 0 ? kEpiAccel : kEpiVjp;
         a.out = ctx->tune[1].p;
@@ -89,9 +92,11 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
             if (ms < best_ms * 0.99f) { best_ms = ms; best = TuneEntry{pol, tab[k].nt, tab[k].r, jt, 0}; }
         }
     }
-    // refine the tile and split around the winner
+    // refine the tile and split around the winner (the pair-symmetric
+    // policy has neither: its table entries are its shapes)
     const TuneEntry base = best;
     for (int jt : {64, 128, 256}) {
+        if (base.pol == kPolSym) break;
         for (int sm : {-1, 0, 1}) {
             if (jt == base.jt && sm == 0) continue;
             if (npad % jt) continue;
@@ -182,6 +187,15 @@ nb_status nb_get_run_path(nb_ctx *ctx, int64_t n, int *out3) {
     out3[0] = path;
     out3[1] = size;
     out3[2] = ctx->run_path == 0 && ctx->tuned.count(tune_key(ctx, 0, n) + "|run") ? 1 : 0;
+    return NB_OK;
+}
+
+nb_status nb_get_form(nb_ctx *ctx, int64_t n, int mode, int *form) {
+    if (!ctx || !form) return NB_ERR_INVALID;
+    if (mode < 0 || mode > 2) return fail(ctx, NB_ERR_INVALID, "mode must be 0, 1 or 2");
+    Shape s;
+    NB_TRY(choose_shape(ctx, mode, std::max<int64_t>(n, 1), &s, nullptr));
+    *form = s.pol;  // the policy ids are the nb_form values
     return NB_OK;
 }
 

@@ -18,6 +18,7 @@ const ForceEntry *table_vjp(int *count);
 const ForceEntry *table_vjp_comp(int *count);
 const ForceEntry *table_div(int *count);
 const ForceEntry *table_pow(int *count);
+const ForceEntry *table_sym(int *count);
 
 const ForceEntry *force_table(int pol, int *count) {
     switch (pol) {
@@ -29,6 +30,7 @@ const ForceEntry *force_table(int pol, int *count) {
         case kPolVjpComp: return table_vjp_comp(count);
         case kPolDiv: return table_div(count);
         case kPolPow: return table_pow(count);
+        case kPolSym: return table_sym(count);
         default: *count = 0; return nullptr;
     }
 }
@@ -168,6 +170,7 @@ int mode_pol(const nb_ctx *ctx, int mode) {
 }
 
 Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_mode, int64_t n) {
+    if (pol == kPolSym) return Shape{pol, nt, r, 1, nt * r};  // no split: items are block pairs
     const ForceEntry *e = find_entry(pol, nt, r);
     const int64_t npad = round_up(std::max<int64_t>(n, 1), kPadBodies);
     const int ntiles = (int)(npad / jt);
@@ -180,9 +183,18 @@ Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_
 }
 
 // Built-in choice when no tuning entry exists.
-Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n) {
+Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     const int pol = mode_pol(ctx, mode);
     int nt = 128, r = 1, jt = 64;
+    if (pol == kPolF32x2 && allow_sym && n >= 32768) {
+        // each unordered pair once, blocks of 1024 bodies from 2^17 up (enough
+        // block pairs to fill the GPU), 512 below; the one-sided policy above
+        // the partial-buffer cap
+        const int snt = n >= 131072 ? 128 : 64;
+        const int64_t b = (int64_t)snt * kSymR, np = round_up(n, b);
+        if ((size_t)(np / b) * 3 * (size_t)np * 4 <= kSymMaxPartBytes)
+            return Shape{kPolSym, snt, kSymR, 1, (int)b};
+    }
     if (pol == kPolF32x2) {
         if (n >= 32768) { r = 4; jt = 128; }
         else if (n >= 4096) { r = 2; jt = 128; }
@@ -207,7 +219,7 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
     const int *o = ctx->p.tile_override;
     const int pol = mode_pol(ctx, mode);
     if (mode != 2 && (o[0] || o[1] || o[2] || o[3])) {
-        Shape h = heuristic_shape(ctx, mode, n);
+        Shape h = heuristic_shape(ctx, mode, n, false);  // overrides address the one-sided kernels
         int nt = o[0] ? o[0] : h.nt, r = o[1] ? o[1] : h.r, jt = o[3] ? o[3] : h.jt;
         if (!find_entry(pol, nt, r))
             return fail(ctx, NB_ERR_UNSUPPORTED, "no compiled kernel for %d threads x %d bodies", nt, r);
@@ -218,15 +230,20 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
         *out = s;
         return NB_OK;
     }
+    if (pol == kPolF32x2 && ctx->form_pin >= 512) {
+        *out = Shape{kPolSym, ctx->form_pin / kSymR, kSymR, 1, ctx->form_pin};
+        return NB_OK;
+    }
     auto it = ctx->tuned.find(tune_key(ctx, mode, n));
     if (mode != 2 && ctx->math == 0 && it != ctx->tuned.end() &&
-        find_entry(it->second.pol, it->second.nt, it->second.r)) {
+        find_entry(it->second.pol, it->second.nt, it->second.r) &&
+        !(ctx->form_pin == 1 && it->second.pol == kPolSym)) {
         const TuneEntry &t = it->second;
         *out = finish_shape(ctx, t.pol, t.nt, t.r, t.jt, t.split_mode, n);
         if (from_tune) *from_tune = true;
         return NB_OK;
     }
-    *out = heuristic_shape(ctx, mode, n);
+    *out = heuristic_shape(ctx, mode, n, ctx->form_pin != 1);
     return NB_OK;
 }
 
@@ -237,6 +254,18 @@ nb_status make_plan(nb_ctx *ctx, const Shape &s, int64_t n, Plan *p) {
     p->s = s;
     p->e = find_entry(s.pol, s.nt, s.r);
     if (!p->e) return fail(ctx, NB_ERR_UNSUPPORTED, "no kernel for shape");
+    if (s.pol == kPolSym) {
+        // blocks of nt x r bodies; partials P[nb][3][npad] (csrc/k_sym.cu)
+        const int64_t b = (int64_t)s.nt * s.r;
+        p->npad = round_up(std::max<int64_t>(n, 1), b);
+        p->iblocks = (int)(p->npad / b);
+        p->ntiles = p->iblocks;
+        p->part_bytes = (size_t)p->iblocks * 3 * (size_t)p->npad * 4;
+        if (p->part_bytes > kSymMaxPartBytes)
+            return fail(ctx, NB_ERR_UNSUPPORTED, "pair-symmetric partials for %lld bodies exceed %zu bytes",
+                        (long long)n, kSymMaxPartBytes);
+        return NB_OK;
+    }
     p->npad = round_up(std::max<int64_t>(n, 1), kPadBodies);
     p->iblocks = iblocks_of(std::max<int64_t>(n, 1), s.nt, s.r);
     p->ntiles = (int)(p->npad / s.jt);
@@ -275,18 +304,18 @@ ForceArgs base_args(nb_ctx *ctx, const Plan &p, int64_t n, const float4 *src) {
 
 nb_status launch_force(nb_ctx *ctx, const Plan &p, const ForceArgs &a, cudaStream_t st) {
     NB_CUDA(p.e->launch(p.s.jt, a, st));
-    ctx->launches += 1;
+    ctx->launches += p.s.pol == kPolSym ? 2 : 1;  // the pair kernel and its fixed-order sum
     return NB_OK;
 }
 
 nb_status pack(nb_ctx *ctx, int64_t n, int64_t npad, const void *x, const void *v, const void *m,
-               float4 *xm, void *ckpt0, cudaStream_t st) {
+               float4 *xm, void *ckpt0, cudaStream_t st, PadTargets pads) {
     if (f64_state(ctx))
         NB_CUDA(launch_pack_f64(n, npad, (const double *)x, (const double *)v, (const double *)m,
-                                xm, (double *)ckpt0, st));
+                                xm, (double *)ckpt0, pads, st));
     else
         NB_CUDA(launch_pack_f32(n, npad, (const float *)x, (const float *)v, (const float *)m, xm,
-                                (float *)ckpt0, st));
+                                (float *)ckpt0, pads, st));
     ctx->launches += 1;
     return NB_OK;
 }
@@ -411,7 +440,10 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
         int64_t saved = ctx->launches;
         float4 *xm[2] = {(float4 *)ctx->xm[0].p, (float4 *)ctx->xm[1].p};
-        nb_status rs = pack(ctx, n, p.npad, x, v, m, xm[0], ckpt, ctx->side);
+        PadTargets pads;
+        pads.base = xm[1];
+        pads.count = 1;
+        nb_status rs = pack(ctx, n, p.npad, x, v, m, xm[0], ckpt, ctx->side, pads);
         const size_t slot_bytes = (size_t)n * 6 * esize(ctx);
         for (int t = 0; rs == NB_OK && t < steps; ++t) {
             ForceArgs a = base_args(ctx, p, n, xm[t & 1]);

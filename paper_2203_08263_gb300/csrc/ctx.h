@@ -54,6 +54,7 @@ struct nb_ctx {
     int debug = 0;
     int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
     int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one cluster, 3 grid
+    int form_pin = 0;  // FP32 forward: 0 chosen per size, 1 one-sided only, 512/1024 pair-symmetric blocks
     std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;
@@ -112,7 +113,7 @@ const ForceEntry *find_entry(int pol, int nt, int r);
 std::string tune_key(const nb_ctx *ctx, int mode, int64_t n);
 int mode_pol(const nb_ctx *ctx, int mode);
 Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_mode, int64_t n);
-Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n);
+Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym = true);
 nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_tune);
 nb_status make_plan(nb_ctx *ctx, const Shape &s, int64_t n, Plan *p);
 nb_status plan_scratch(nb_ctx *ctx, const Plan &p);
@@ -120,8 +121,10 @@ nb_status plan_scratch(nb_ctx *ctx, const Plan &p);
 // Launches.
 ForceArgs base_args(nb_ctx *ctx, const Plan &p, int64_t n, const float4 *src);
 nb_status launch_force(nb_ctx *ctx, const Plan &p, const ForceArgs &a, cudaStream_t st);
+// Pack (x, m) into xm (zero-mass padding up to npad); `pads` names the
+// buffers the following step epilogues write, whose padding is zeroed too.
 nb_status pack(nb_ctx *ctx, int64_t n, int64_t npad, const void *x, const void *v, const void *m,
-               float4 *xm, void *ckpt0, cudaStream_t st);
+               float4 *xm, void *ckpt0, cudaStream_t st, PadTargets pads = PadTargets());
 GraphEntry *graph_lookup(nb_ctx *ctx, const std::string &key);
 void graph_insert(nb_ctx *ctx, const std::string &key, cudaGraphExec_t ex, int64_t nodes);
 // Which nb_run path serves n bodies: *path = 1 graph of force launches,

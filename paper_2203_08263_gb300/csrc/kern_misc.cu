@@ -16,9 +16,14 @@ inline unsigned blocks_for(int64_t n) {
 template <class TS>
 __global__ void pack_kernel(int64_t n, int64_t npad, const TS *__restrict__ x,
                             const TS *__restrict__ v, const TS *__restrict__ m, float4 *xm,
-                            TS *ckpt0) {
+                            TS *ckpt0, PadTargets pads) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npad) return;
+    // the step epilogues repack only real bodies, so the buffers they write
+    // get their zero-mass padding here (a buffer reused from a larger system
+    // would otherwise keep that system's bodies in its padding)
+    if (i >= n)
+        for (int s = 0; s < pads.count; ++s) pair_put(pads.base + s * pads.stride, i, 0.f, 0.f, 0.f, 0.f);
     if (i < n) {
         const TS x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
         pair_put(xm, i, (float)x0, (float)x1, (float)x2, (float)m[i]);
@@ -168,14 +173,16 @@ __global__ void copy_ckpt_kernel(int64_t n, const TS *__restrict__ slot, TS *x, 
 }  // namespace
 
 cudaError_t launch_pack_f32(int64_t n, int64_t npad, const float *x, const float *v,
-                            const float *m, float4 *xm, float *ckpt0, cudaStream_t st) {
-    pack_kernel<float><<<blocks_for(npad), kThreads, 0, st>>>(n, npad, x, v, m, xm, ckpt0);
+                            const float *m, float4 *xm, float *ckpt0, PadTargets pads,
+                            cudaStream_t st) {
+    pack_kernel<float><<<blocks_for(npad), kThreads, 0, st>>>(n, npad, x, v, m, xm, ckpt0, pads);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_f64(int64_t n, int64_t npad, const double *x, const double *v,
-                            const double *m, float4 *xm, double *ckpt0, cudaStream_t st) {
-    pack_kernel<double><<<blocks_for(npad), kThreads, 0, st>>>(n, npad, x, v, m, xm, ckpt0);
+                            const double *m, float4 *xm, double *ckpt0, PadTargets pads,
+                            cudaStream_t st) {
+    pack_kernel<double><<<blocks_for(npad), kThreads, 0, st>>>(n, npad, x, v, m, xm, ckpt0, pads);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,17 @@ enum Pol : int {
     kPolVjpComp = 5, // adjoint VJP, compensated, FP64 state
     kPolDiv = 6,     // ablation: sqrt + division
     kPolPow = 7,     // ablation: powf
-    kPolCount = 8
+    kPolSym = 8,     // plain FP32 forces, each unordered pair once (csrc/k_sym.cu)
+    kPolCount = 9
 };
+
+// Bodies per lane of the pair-symmetric policy; its table holds blocks of
+// 32 x R x (2 or 4 warps) = 512 or 1024 bodies (Shape: nt = 64 or 128, r = R,
+// jt = the block, split = 1).
+constexpr int kSymR = 8;
+// The pair-symmetric policy keeps one partial per body and partner block,
+// nb x 3 x npad floats; above this many bytes the one-sided policy serves.
+constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
 
 struct Shape {
     int pol, nt, r, split, jt;
@@ -41,10 +50,19 @@ inline size_t force_smem_bytes(int rec_f4, int jt) {
 }
 
 // ---- O(n) helpers (kern_misc.cu)
+// Further packed buffers (count of them, `stride` float4 apart from `base`)
+// whose padding records [n, npad) the pack also zeroes.
+struct PadTargets {
+    float4 *base = nullptr;
+    int count = 0;
+    int64_t stride = 0;
+};
 cudaError_t launch_pack_f32(int64_t n, int64_t npad, const float *x, const float *v,
-                            const float *m, float4 *xm, float *ckpt0, cudaStream_t st);
+                            const float *m, float4 *xm, float *ckpt0, PadTargets pads,
+                            cudaStream_t st);
 cudaError_t launch_pack_f64(int64_t n, int64_t npad, const double *x, const double *v,
-                            const double *m, float4 *xm, double *ckpt0, cudaStream_t st);
+                            const double *m, float4 *xm, double *ckpt0, PadTargets pads,
+                            cudaStream_t st);
 // synthetic bodies for tuning runs
 cudaError_t launch_fill_synthetic(int64_t n, int64_t npad, float4 *xm, int rec_f4,
                                   cudaStream_t st);

@@ -104,7 +104,7 @@ extern "C" nb_status nb_accel_noalloc(int64_t n, const float *x, const float *m,
         cudaGetLastError();
         return NB_ERR_CUDA;
     }
-    if (launch_pack_f32(n, npad, x, nullptr, m, xm, nullptr, st) != cudaSuccess) {
+    if (launch_pack_f32(n, npad, x, nullptr, m, xm, nullptr, PadTargets(), st) != cudaSuccess) {
         cudaGetLastError();
         return NB_ERR_CUDA;
     }

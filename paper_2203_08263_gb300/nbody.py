@@ -21,7 +21,11 @@ NB_OK, NB_ERR_INVALID, NB_ERR_CUDA, NB_ERR_NOMEM, NB_ERR_TIMEOUT, NB_ERR_UNSUPPO
 NB_FP32, NB_FP32_COMP_FP64_STATE = 0, 1
 NB_SCHEME_PAPER, NB_SCHEME_KDK = 0, 1
 NB_DBG_WAIT_TIMEOUT_NS, NB_DBG_STALL_PRODUCER, NB_DBG_MATH_VARIANT, NB_DBG_RUN_PATH = 1, 2, 3, 4
+NB_DBG_FORM = 5
 MODE_FORWARD, MODE_ADJOINT, MODE_POTENTIAL = 0, 1, 2
+# nb_form values (nb_get_form)
+FORMS = {0: "f32x2", 1: "scalar", 2: "compensated", 3: "potential", 4: "vjp",
+         5: "vjp_compensated", 6: "sqrt_div", 7: "pow", 8: "pair_symmetric"}
 
 # Every symbol include/nbody.h declares, with (restype, argtypes).
 _c = ctypes
@@ -54,6 +58,7 @@ SIGNATURES = {
     "nb_energy": (_i, [_vp, _i64, _vp, _vp, _vp, _c.POINTER(_d), _vp]),
     "nb_autotune": (_i, [_vp, _i64, _i]),
     "nb_get_config": (_i, [_vp, _i64, _i, _c.POINTER(_i)]),
+    "nb_get_form": (_i, [_vp, _i64, _i, _c.POINTER(_i)]),
     "nb_sync": (_i, [_vp, _vp]),
     "nb_launch_count": (_i64, [_vp]),
     "nb_debug_set": (_i, [_vp, _i, _i64]),
@@ -252,8 +257,10 @@ class Context:
     def get_config(self, n: int, mode: int = MODE_FORWARD) -> dict:
         out = (_i * 5)()
         self._check(self.lib.nb_get_config(self.h, int(n), int(mode), out), "nb_get_config")
+        form = _i()
+        self._check(self.lib.nb_get_form(self.h, int(n), int(mode), ctypes.byref(form)), "nb_get_form")
         return {"threads": out[0], "bodies_per_thread": out[1], "split": out[2], "jtile": out[3],
-                "tuned": bool(out[4])}
+                "tuned": bool(out[4]), "form": FORMS.get(form.value, str(form.value))}
 
     def sync(self, stream=None):
         self._check(self.lib.nb_sync(self.h, self._s(stream)), "nb_sync")

@@ -2,6 +2,7 @@
 
     python -m paper_2203_08263_gb300.profile_case --n 65536 --shape 128,4,16,256 --pol fp32
     python -m paper_2203_08263_gb300.profile_case --n 1024 --pol step --steps 100 --path 2
+    python -m paper_2203_08263_gb300.profile_case --n 262144 --pol step --steps 3 --form 1024
     python -m paper_2203_08263_gb300.profile_case --peaks
 
 Input: Plummer sphere (seed 1), eps = 0.05. Prints the CUDA-event time per
@@ -26,14 +27,16 @@ def main():
     ap.add_argument("--steps", type=int, default=1, help="paper steps per call for --pol step / step-comp")
     ap.add_argument("--path", type=int, default=0,
                     help="nb_run path for --pol step / step-comp: 0 chosen per size, 1 graph, 2 one cluster")
+    ap.add_argument("--form", type=int, default=0,
+                    help="FP32 force form: 0 chosen per size, 1 one-sided, 512/1024 pair-symmetric blocks")
     ap.add_argument("--peaks", action="store_true")
     a = ap.parse_args()
 
     import torch
 
     from paper_2203_08263_gb300 import build, ics
-    from paper_2203_08263_gb300.nbody import (MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, NB_DBG_RUN_PATH,
-                                              Context)
+    from paper_2203_08263_gb300.nbody import (MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, NB_DBG_FORM,
+                                              NB_DBG_RUN_PATH, Context)
 
     build.build()
     if a.peaks:
@@ -48,6 +51,7 @@ def main():
     s = ics.plummer(a.n, seed=1)
     ctx = Context(1.0, 0.05, 1e-3, precision=prec, tile_override=shape)
     ctx.debug_set(NB_DBG_RUN_PATH, a.path)
+    ctx.debug_set(NB_DBG_FORM, a.form)
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,

@@ -209,12 +209,15 @@ def test_c3_run_fp64_state(nbm):
     assert rel_l2(to_np(v), vr) <= 1e-6
 
 
-def test_c2_full_size_sampled(nbm):
+@pytest.mark.parametrize("form", [0, 1])
+def test_c2_full_size_sampled(nbm, form):
     """Single large system: N=262144 Plummer (seed 1), eps=0.05, FP32;
-    sampled outputs against the oracle."""
+    sampled outputs against the oracle, in the form chosen for the size (the
+    pair-symmetric kernel untuned) and in the one-sided form."""
     n, G, eps = 262144, 1.0, 0.05
     s = ics.plummer(n, seed=1)
     ctx = nbm.Context(G, eps, 1e-3)
+    ctx.debug_set(nbm.NB_DBG_FORM, form)
     a = to_np(ctx.accel(_t(s.x), _t(s.m)))
     idx = ics.subset_indices(n, 1024, 77)
     assert rel_l2(a[idx], oracle.accel(s.x, s.m, G, eps, idx)) <= 2e-5

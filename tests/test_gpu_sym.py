@@ -1,0 +1,169 @@
+"""GPU parity of the pair-symmetric FP32 force form (each unordered pair once,
+both bodies updated with opposite signs) against the FP64 oracle, through the
+C-ABI: accelerations (<= 2e-5 relative L2), runs of both update schemes,
+checkpoints, determinism, the adjoint's recompute, and the padding of the
+step buffers."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_08263_gb300 import ics
+from gpu_util import ensure_built, rel_l2, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GRAPH = 1
+
+
+@pytest.fixture(scope="module")
+def nbm():
+    ensure_built()
+    from paper_2203_08263_gb300 import nbody
+    return nbody
+
+
+def _t(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _ctx(nbm, block, G=1.0, eps=0.01, dt=1e-3, scheme="paper"):
+    ctx = nbm.Context(G, eps, dt, scheme=scheme)
+    ctx.debug_set(nbm.NB_DBG_FORM, block)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+    return ctx
+
+
+# one body (the diagonal item alone), odd sizes, one and several blocks with
+# ragged padding, exact multiples of the block
+@pytest.mark.parametrize("block", [512, 1024])
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 511, 512, 513, 1000, 1024, 2047, 3001, 5120])
+def test_sym_accel_matches_oracle(nbm, block, n):
+    G, eps = 0.9, 0.02
+    s = ics.cube(n, seed=300 + n)
+    ctx = _ctx(nbm, block, G, eps)
+    assert ctx.get_config(n)["form"] == "pair_symmetric"
+    a = to_np(ctx.accel(_t(s.x), _t(s.m)))
+    ref = oracle.accel(s.x, s.m, G, eps)
+    if n == 1:
+        assert np.all(a == 0.0)
+    else:
+        assert rel_l2(a, ref) <= 2e-5
+
+
+def test_sym_accel_plummer_momentum(nbm):
+    """Plummer sphere (the large-system workload's distribution): forces
+    against the oracle, and the pair antisymmetry of the form itself: the
+    mass-weighted sum of the forces is zero up to FP32 rounding of the sums."""
+    n, G, eps = 20000, 1.0, 0.05
+    s = ics.plummer(n, seed=5)
+    ctx = _ctx(nbm, 1024, G, eps)
+    a = to_np(ctx.accel(_t(s.x), _t(s.m)))
+    assert rel_l2(a, oracle.accel(s.x, s.m, G, eps)) <= 2e-5
+    p = (s.m[:, None] * a).sum(axis=0)
+    scale = (s.m[:, None] * np.abs(a)).sum(axis=0)
+    assert np.all(np.abs(p) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("scheme", ["paper", "kdk"])
+@pytest.mark.parametrize("n", [777, 4096])
+def test_sym_run_matches_oracle(nbm, scheme, n):
+    s = ics.cube(n, seed=40 + n)
+    ctx = _ctx(nbm, 512, G=1.0, eps=0.01, dt=1e-3, scheme=scheme)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    before = ctx.launch_count
+    ctx.run(x, v, m, 10)
+    ctx.sync()
+    # pack + (pair kernel + fixed-order sum) per step (+ the closing half kick)
+    assert ctx.launch_count - before == 1 + 2 * (10 + (scheme == "kdk"))
+    xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 10, scheme=scheme)
+    assert rel_l2(to_np(x), xr) <= 1e-5
+    assert rel_l2(to_np(v), vr) <= 1e-4
+
+
+def test_sym_checkpoints_and_one_sided_agree(nbm):
+    n, steps, k = 3000, 12, 4
+    s = ics.cube(n, seed=9)
+    out = {}
+    for form in (1, 1024):
+        ctx = _ctx(nbm, form)
+        x, v, m = _t(s.x), _t(s.v), _t(s.m)
+        ck = torch.zeros((steps // k + 1, n, 6), dtype=torch.float32, device=DEV)
+        ctx.run(x, v, m, steps, ckpt=ck, ckpt_every=k)
+        ctx.sync()
+        out[form] = (to_np(x), to_np(v), to_np(ck))
+    xs, vs, cs = out[1024]
+    xo, vo, co = out[1]
+    assert rel_l2(xs, xo) <= 1e-6 and rel_l2(vs, vo) <= 1e-5
+    for slot in range(steps // k + 1):
+        assert rel_l2(cs[slot], co[slot]) <= 1e-5
+    assert np.array_equal(cs[-1][:, :3], xs) and np.array_equal(cs[-1][:, 3:], vs)
+
+
+def test_sym_is_deterministic(nbm):
+    n = 6000
+    s = ics.plummer(n, seed=3)
+    ctx = _ctx(nbm, 512, eps=0.05)
+    a1 = ctx.accel(_t(s.x), _t(s.m)).clone()
+    a2 = ctx.accel(_t(s.x), _t(s.m)).clone()
+    ctx.sync()
+    assert torch.equal(a1, a2)
+
+
+def test_default_form_by_size(nbm):
+    """Untuned FP32 forward: one-sided below 32768 bodies, pair-symmetric
+    from there; the precision form and the pinned one-sided form never take
+    it."""
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    if ctx.get_config(40000)["tuned"]:
+        pytest.skip("a tuning table is loaded")
+    assert ctx.get_config(20000)["form"] == "f32x2"
+    assert ctx.get_config(40000)["form"] == "pair_symmetric"
+    ctx.debug_set(nbm.NB_DBG_FORM, 1)
+    assert ctx.get_config(40000)["form"] == "f32x2"
+    comp = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
+    assert comp.get_config(40000)["form"] == "compensated"
+
+
+def test_sym_adjoint_matches_one_sided(nbm):
+    """nb_adjoint recomputes each checkpoint segment with the forward force
+    form: gradients with the pair-symmetric recompute agree with the
+    one-sided ones."""
+    n, T, k = 700, 12, 4
+    s = ics.cube(n, seed=4)
+    rng = np.random.default_rng(1)
+    target = rng.uniform(-1, 1, (n, 3))
+    grads = {}
+    for form in (1, 512):
+        ctx = _ctx(nbm, form)
+        x0, v0, m = _t(s.x), _t(s.v), _t(s.m)
+        ck = torch.zeros((T // k + 1, n, 6), dtype=torch.float32, device=DEV)
+        x, v = x0.clone(), v0.clone()
+        ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+        xbar = 2 * (x - _t(target))
+        vbar = torch.zeros_like(v)
+        g = ctx.adjoint(m, T, ck, k, xbar, vbar)
+        ctx.sync()
+        grads[form] = [to_np(t) for t in g]
+    for a, b in zip(grads[512], grads[1]):
+        assert rel_l2(a, b) <= 1e-5
+
+
+@pytest.mark.parametrize("form", [1, 512])
+def test_step_buffer_padding_not_stale(nbm, form):
+    """A context reused for a smaller system of the same padded size: the
+    padding of the buffers that the steps write must not keep the larger
+    system's bodies (they would act as extra masses from the second step)."""
+    ctx = _ctx(nbm, form)
+    big = ics.cube(1024, seed=11)
+    x, v, m = _t(big.x), _t(big.v), _t(big.m * 50)
+    ctx.run(x, v, m, 3)
+    ctx.sync()
+    n = 1000
+    s = ics.cube(n, seed=12)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    ctx.run(x, v, m, 6)
+    ctx.sync()
+    xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 6)
+    assert rel_l2(to_np(x), xr) <= 1e-5
+    assert rel_l2(to_np(v), vr) <= 1e-4
