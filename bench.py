@@ -175,6 +175,9 @@ def run_reference(args):
 # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch each, on this
 # GPU type. Most of it is split partials evicted from L2; the O(N) state is
 # 21 MB. Reported only when the bench runs one of these shapes.
+# The pair-symmetric kernel (threads, 8, 1, block) writes nb x 3 x npad floats
+# of block-pair partials (0.8 GB at N = 262144); its entry is scaled from a
+# capture at N = 131072 by (262144 / 131072)^2 (the partials grow as N^2).
 STEP_TRAFFIC_BYTES = {
     (128, 8, 19, 128): 11.85e6 + 34.15e6,
     (128, 8, 19, 64): 11.07e6 + 34.31e6,
@@ -186,6 +189,17 @@ STEP_TRAFFIC_BYTES = {
 
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # unit counts x maximum SM clock
+
+# FP32 lane operations per ordered interaction, by force form: the one-sided
+# kernel spends 3 subtractions, 3 multiply-adds for s, 3 multiplies for
+# m s^-3/2 and 3 multiply-adds into a (12); the pair-symmetric kernel spends
+# 16 per unordered pair (d, s and s^-3/2 shared), 8 per ordered interaction.
+OPS_PER_INTERACTION = {"f32x2": 12, "scalar": 12, "pair_symmetric": 8}
+KERNEL_NAME = {"f32x2": "force_kernel<AccelF32x2> (+ its 1-launch pack, <0.1% of the step)",
+               "scalar": "force_kernel<AccelScalar> (+ its 1-launch pack)",
+               "pair_symmetric": "sym_force_kernel (+ sym_finish_kernel, the fixed-order sum of the "
+                                 "block-pair partials with the kick/drift epilogue, and the pack: "
+                                 "timed together, so the kernel's own rate is slightly higher)"}
 
 
 def fp32_peak_tflops(props, sm_max_mhz):
@@ -277,15 +291,24 @@ def run_ours(args):
 
     props = torch.cuda.get_device_properties(dev)
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(props, sm_max)
-    achieved = FLOPS_PER_INTERACTION * inter / (ms_step / 1e3) / 1e12
+    peak_20 = fp32_peak_tflops(props, sm_max)
+    form = cfg.get("form", "f32x2")
+    ops = OPS_PER_INTERACTION.get(form, 12)
+    # the FP32 pipe's roofline: lane operations the form executes per second
+    # against 128 lanes per SM per clock
+    lane_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    achieved = ops * inter / (ms_step / 1e3) / 1e12
     shape_key = (cfg["threads"], cfg["bodies_per_thread"], cfg["split"], cfg["jtile"])
     traffic = STEP_TRAFFIC_BYTES.get(shape_key) if n == 262144 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
-                              "(max SM clock); 20 flops per interaction",
-                "kernel": "force_kernel<AccelF32x2> (+ its 1-launch pack, <0.1% of the step)"}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": lane_peak, "unit": "T FP32 lane-ops/s",
+                "frac": achieved / lane_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                              f"(max SM clock); {ops} lane operations per interaction in the {form} form",
+                "kernel": KERNEL_NAME.get(form, form),
+                "pct_fp32_peak_20flop": 100.0 * FLOPS_PER_INTERACTION * inter / (ms_step / 1e3) / 1e12 / peak_20,
+                "pct_basis": f"20 flops per interaction (Section 4.1) over {peak_20:.2f} TFLOP/s "
+                             "(2 flops per FMA lane); above the one-sided form's 83.3 % ceiling when "
+                             "each pair term feeds two bodies"}
 
     # end to end through the public C-ABI with host buffers: the call copies
     # the state in, runs the step, copies it back and returns

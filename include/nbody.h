@@ -119,7 +119,10 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  * of partials in the context (nb = npad / 1024 blocks of 1024 bodies,
  * npad = n rounded up to a block: about 12 n^2 / 1024 bytes, 0.8 GB at
  * n = 262144); systems whose partials would exceed 8 GiB use the one-sided
- * kernel. Results are deterministic in every form.
+ * kernel. The FP32 VJP of nb_vjp and nb_adjoint has the same two forms (the
+ * pair-symmetric one from n = 8192, blocks of 256 or 512 bodies, 8 sums per
+ * body: about 32 n^2 / 256 bytes of partials at n < 65536). Results are
+ * deterministic in every form.
  */
 nb_status nb_accel(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a,
                    void *stream);
@@ -252,7 +255,8 @@ typedef enum {
     NB_FORM_VJP_COMPENSATED = 5, /* adjoint VJP, compensated, FP64 state */
     NB_FORM_SQRT_DIV = 6,        /* ablation: sqrt then division */
     NB_FORM_POW = 7,             /* ablation: powf */
-    NB_FORM_PAIR_SYMMETRIC = 8   /* FP32, each unordered pair once */
+    NB_FORM_PAIR_SYMMETRIC = 8,  /* FP32, each unordered pair once */
+    NB_FORM_VJP_PAIR_SYMMETRIC = 9 /* adjoint VJP, FP32, each unordered pair once */
 } nb_form;
 
 /* The force-sum form (nb_form) the context would use for (n, mode), mode as
@@ -299,7 +303,11 @@ typedef enum {
      * kernels only, 512 or 1024 = the pair-symmetric kernel with blocks of
      * that many bodies at every size (nb_run's graph path; the fused
      * small-system paths keep their own kernel). */
-    NB_DBG_FORM = 5
+    NB_DBG_FORM = 5,
+    /* FP32 VJP form (nb_vjp, nb_adjoint): 0 = chosen per size (default),
+     * 1 = one-sided only, 256 or 512 = the pair-symmetric kernel with blocks
+     * of that many bodies at every size. */
+    NB_DBG_VJP_FORM = 6
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 

@@ -249,9 +249,18 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         return NB_OK;
     }
     if (key == NB_DBG_FORM) {
-        if (value != 0 && value != 1 && value != 512 && value != 1024)
-            return fail(ctx, NB_ERR_INVALID, "force form must be 0, 1, 512 or 1024");
+        if (value != 0 && value != 1 &&
+            !(value % kSymR == 0 && find_entry(kPolSym, (int)(value / kSymR), kSymR)))
+            return fail(ctx, NB_ERR_INVALID, "force form must be 0, 1 or a compiled pair-symmetric block (512, 1024)");
         ctx->form_pin = (int)value;
+        clear_graphs(ctx);
+        return NB_OK;
+    }
+    if (key == NB_DBG_VJP_FORM) {
+        if (value != 0 && value != 1 &&
+            !(value % kSymVjpR == 0 && find_entry(kPolVjpSym, (int)(value / kSymVjpR), kSymVjpR)))
+            return fail(ctx, NB_ERR_INVALID, "VJP form must be 0, 1 or a compiled pair-symmetric block (256, 512)");
+        ctx->vjp_form_pin = (int)value;
         clear_graphs(ctx);
         return NB_OK;
     }

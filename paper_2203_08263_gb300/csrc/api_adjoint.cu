@@ -94,7 +94,8 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
     NB_TRY(ensure(ctx, ctx->counters, (size_t)pv.iblocks * 4, true));
     NB_TRY(ensure(ctx, ctx->part2, pf.part_bytes));
     NB_TRY(ensure(ctx, ctx->counters2, (size_t)pf.iblocks * 4, true));
-    const int64_t npad = pf.npad;
+    // the records of both kernels live in buffers of the larger padding
+    const int64_t npad = std::max(pf.npad, pv.npad);
     const int k = ckpt_every;
     const bool f64 = f64_state(ctx);
     NB_TRY(ensure(ctx, ctx->rec, (size_t)npad * 8 * pol_rec_f4(sv.pol)));

@@ -24,8 +24,10 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
         if (f64_state(ctx)) pols = {kPolComp};
         else if (ctx->math == 0 && n >= 8192) pols = {kPolF32x2, kPolScalar, kPolSym};
         else pols = {kPolF32x2, kPolScalar};
+    } else if (f64_state(ctx)) {
+        pols = {kPolVjpComp};
     } else {
-        pols = {f64_state(ctx) ? kPolVjpComp : kPolVjp};
+        pols = n >= 2048 ? std::vector<int>{kPolVjp, kPolVjpSym} : std::vector<int>{kPolVjp};
     }
     const int64_t npad = round_up(n, kPadBodies);
     const size_t es = esize(ctx);
@@ -43,7 +45,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     auto time_shape = [&](const Shape &s, float *ms) -> nb_status {
         Plan p;
         NB_TRY(make_plan(ctx, s, n, &p));
-        const size_t cap = s.pol == kPolSym ? kSymMaxPartBytes : ((size_t)1 << 31);
+        const size_t cap = pol_is_sym(s.pol) ? kSymMaxPartBytes : ((size_t)1 << 31);
         if (p.part_bytes > cap) { *ms = 1e30f; return NB_OK; }
         NB_TRY(plan_scratch(ctx, p));
         NB_CUDA(launch_fill_synthetic(n, p.npad, (float4 *)ctx->tune[0].p, pol_rec_f4(s.pol), st));
@@ -96,7 +98,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     // policy has neither: its table entries are its shapes)
     const TuneEntry base = best;
     for (int jt : {64, 128, 256}) {
-        if (base.pol == kPolSym) break;
+        if (pol_is_sym(base.pol)) break;
         for (int sm : {-1, 0, 1}) {
             if (jt == base.jt && sm == 0) continue;
             if (npad % jt) continue;

@@ -19,6 +19,7 @@ const ForceEntry *table_vjp_comp(int *count);
 const ForceEntry *table_div(int *count);
 const ForceEntry *table_pow(int *count);
 const ForceEntry *table_sym(int *count);
+const ForceEntry *table_vjp_sym(int *count);
 
 const ForceEntry *force_table(int pol, int *count) {
     switch (pol) {
@@ -31,10 +32,13 @@ const ForceEntry *force_table(int pol, int *count) {
         case kPolDiv: return table_div(count);
         case kPolPow: return table_pow(count);
         case kPolSym: return table_sym(count);
+        case kPolVjpSym: return table_vjp_sym(count);
         default: *count = 0; return nullptr;
     }
 }
-int pol_rec_f4(int pol) { return pol == kPolVjp ? 4 : (pol == kPolVjpComp ? 5 : 2); }
+int pol_rec_f4(int pol) {
+    return (pol == kPolVjp || pol == kPolVjpSym) ? 4 : (pol == kPolVjpComp ? 5 : 2);
+}
 int pol_part_f4(int pol) {
     switch (pol) {
         case kPolComp: return 2;
@@ -170,7 +174,7 @@ int mode_pol(const nb_ctx *ctx, int mode) {
 }
 
 Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_mode, int64_t n) {
-    if (pol == kPolSym) return Shape{pol, nt, r, 1, nt * r};  // no split: items are block pairs
+    if (pol_is_sym(pol)) return Shape{pol, nt, r, 1, nt * r};  // no split: items are block pairs
     const ForceEntry *e = find_entry(pol, nt, r);
     const int64_t npad = round_up(std::max<int64_t>(n, 1), kPadBodies);
     const int ntiles = (int)(npad / jt);
@@ -207,6 +211,14 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     } else if (pol == kPolPot) {
         r = 2;
         if (n >= 4096) jt = 128;
+    } else if (pol == kPolVjp && allow_sym && n >= 8192) {
+        // each unordered pair once: blocks of 256 bodies below 2^16, 512 from there
+        const int snt = n >= 65536 ? 128 : 64;
+        const int64_t b = (int64_t)snt * kSymVjpR, np = round_up(n, b);
+        if ((size_t)(np / b) * 8 * (size_t)np * 4 <= kSymMaxPartBytes)
+            return Shape{kPolVjpSym, snt, kSymVjpR, 1, (int)b};
+        r = 2;
+        jt = 128;
     } else {  // VJP (the precision form's R = 2 instance spills at the 128-register cap)
         r = (n >= 8192 && pol == kPolVjp) ? 2 : 1;
         if (n >= 4096) jt = 128;
@@ -230,20 +242,25 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
         *out = s;
         return NB_OK;
     }
-    if (pol == kPolF32x2 && ctx->form_pin >= 512) {
+    if (pol == kPolF32x2 && ctx->form_pin > 1) {
         *out = Shape{kPolSym, ctx->form_pin / kSymR, kSymR, 1, ctx->form_pin};
         return NB_OK;
     }
+    if (pol == kPolVjp && ctx->vjp_form_pin > 1) {
+        *out = Shape{kPolVjpSym, ctx->vjp_form_pin / kSymVjpR, kSymVjpR, 1, ctx->vjp_form_pin};
+        return NB_OK;
+    }
+    const int pin = mode == 1 ? ctx->vjp_form_pin : ctx->form_pin;
     auto it = ctx->tuned.find(tune_key(ctx, mode, n));
     if (mode != 2 && ctx->math == 0 && it != ctx->tuned.end() &&
         find_entry(it->second.pol, it->second.nt, it->second.r) &&
-        !(ctx->form_pin == 1 && it->second.pol == kPolSym)) {
+        !(pin == 1 && pol_is_sym(it->second.pol))) {
         const TuneEntry &t = it->second;
         *out = finish_shape(ctx, t.pol, t.nt, t.r, t.jt, t.split_mode, n);
         if (from_tune) *from_tune = true;
         return NB_OK;
     }
-    *out = heuristic_shape(ctx, mode, n, ctx->form_pin != 1);
+    *out = heuristic_shape(ctx, mode, n, pin != 1);
     return NB_OK;
 }
 
@@ -254,13 +271,13 @@ nb_status make_plan(nb_ctx *ctx, const Shape &s, int64_t n, Plan *p) {
     p->s = s;
     p->e = find_entry(s.pol, s.nt, s.r);
     if (!p->e) return fail(ctx, NB_ERR_UNSUPPORTED, "no kernel for shape");
-    if (s.pol == kPolSym) {
-        // blocks of nt x r bodies; partials P[nb][3][npad] (csrc/k_sym.cu)
+    if (pol_is_sym(s.pol)) {
+        // blocks of nt x r bodies; partials P[nb][sums][npad] (csrc/k_sym.cu)
         const int64_t b = (int64_t)s.nt * s.r;
         p->npad = round_up(std::max<int64_t>(n, 1), b);
         p->iblocks = (int)(p->npad / b);
         p->ntiles = p->iblocks;
-        p->part_bytes = (size_t)p->iblocks * 3 * (size_t)p->npad * 4;
+        p->part_bytes = (size_t)p->iblocks * sym_sums(s.pol) * (size_t)p->npad * 4;
         if (p->part_bytes > kSymMaxPartBytes)
             return fail(ctx, NB_ERR_UNSUPPORTED, "pair-symmetric partials for %lld bodies exceed %zu bytes",
                         (long long)n, kSymMaxPartBytes);
@@ -304,7 +321,7 @@ ForceArgs base_args(nb_ctx *ctx, const Plan &p, int64_t n, const float4 *src) {
 
 nb_status launch_force(nb_ctx *ctx, const Plan &p, const ForceArgs &a, cudaStream_t st) {
     NB_CUDA(p.e->launch(p.s.jt, a, st));
-    ctx->launches += p.s.pol == kPolSym ? 2 : 1;  // the pair kernel and its fixed-order sum
+    ctx->launches += pol_is_sym(p.s.pol) ? 2 : 1;  // the pair kernel and its fixed-order sum
     return NB_OK;
 }
 

@@ -55,6 +55,7 @@ struct nb_ctx {
     int math = 0;  // ablation of the FP32 forward denominator (0 = MUFU rsqrt)
     int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one cluster, 3 grid
     int form_pin = 0;  // FP32 forward: 0 chosen per size, 1 one-sided only, 512/1024 pair-symmetric blocks
+    int vjp_form_pin = 0;  // FP32 VJP: 0 chosen per size, 1 one-sided only, 256/512 pair-symmetric blocks
     std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;

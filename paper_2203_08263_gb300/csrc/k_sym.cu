@@ -1,14 +1,26 @@
-// Pair-symmetric FP32 force sum: every unordered pair {i, j} is evaluated once
-// and feeds both bodies (Newton's third law: the pair term of j on i is
-// m_j s^-3/2 d and that of i on j is -m_i s^-3/2 d, d = x_j - x_i), so the
-// force sum of Section 2.3 (counted at 20 flops per ordered interaction in
-// Section 4.1) costs 16 FP32 lane operations per unordered pair, 8 per
-// ordered interaction, against 12 in the one-sided policies.
+// Pair-symmetric FP32 pair sums: every unordered pair {i, j} is evaluated once
+// and feeds both bodies.
+//
+// Forces (Section 2.3): the term of j on i is m_j s^-3/2 d and that of i on j
+// is -m_i s^-3/2 d (d = x_j - x_i, s = |d|^2 + eps^2; Newton's third law), so
+// the sum counted at 20 flops per ordered interaction in Section 4.1 costs 16
+// FP32 lane operations per unordered pair, 8 per ordered interaction, against
+// 12 in the one-sided kernel.
+//
+// Adjoint VJP (the reverse step's x-bar and m-bar sums; the one-sided
+// VjpF32x2 policy states them): with f = s^-3/2, h = s^-5/2, e = abar_j . d,
+// g = abar_i . d and c = m_j g - m_i e, body i gathers
+//   U_i += f abar_j,  V_i += f m_j,  W_i += h c d,  P_i += f e
+// and, from the same pair seen from j (d -> -d, e <-> -g, so c is unchanged),
+//   U_j += f abar_i,  V_j += f m_i,  W_j -= h c d,  P_j -= f g;
+// 34 lane operations per unordered pair (d, s, f, h, e, g, c shared) against
+// 2 x 26 one-sided. The VJP's own pair (j == i) is masked: its f = eps^-3
+// terms cancel only in the epilogue's FP32 sums.
 //
 // Work decomposition. Bodies are padded with zero-mass bodies to nb blocks of
 // B = 32 x W x R. An item is a block pair (bi, bj), bi <= bj, one CTA each.
 // Each warp of the CTA owns 32 x R bodies of block bi, R per lane, held
-// duplicated in f32x2 registers as in the one-sided policy; block bj is
+// duplicated in f32x2 registers as in the one-sided kernels; block bj is
 // walked in chunks of 32 records (64 bodies), one record per lane, and for
 // 32 rounds every lane evaluates its R i-bodies against the two bodies of its
 // current record, then passes the record and the record's running j-side sums
@@ -16,13 +28,13 @@
 // its sums over the warp's i-bodies, which land in the warp's slice of shared
 // memory; at the end the CTA adds the W slices in warp order. The diagonal
 // item (bi == bj) evaluates every ordered pair of its block from the i side
-// only (a body with itself contributes exactly 0: d = 0).
+// only.
 //
-// Determinism. The partial sums land in P[p][c][b] (p = the partner block:
-// bj for the i side of item (bi, bj), bi for its j side), which every body
-// fills exactly once for each p; a second kernel adds P[0..nb-1][c][b] in
-// that order and runs the shared epilogue (write a, or kick + drift + repack),
-// so the result does not depend on scheduling.
+// Determinism. The partial sums land in P[p][k][b] (p = the partner block: bj
+// for the i side of item (bi, bj), bi for its j side; k = the sum), which
+// every body fills exactly once for each p; a second kernel adds
+// P[0..nb-1][k][b] in that order and runs the policy's epilogue, so the
+// result does not depend on scheduling.
 #include <cstring>
 
 #include "kernels.h"
@@ -33,6 +45,149 @@ namespace {
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
+
+// Forces.
+struct SymAccel {
+    static constexpr int R = kSymR;
+    static constexpr int NACC = 3;      // a_x, a_y, a_z
+    static constexpr int REC_F4 = 2;    // {x0,x1,y0,y1} {z0,z1,m0,m1}
+    static constexpr bool SELF_MASK = false;  // d = 0 gives exactly 0
+    __host__ __device__ static constexpr float jsign(int) { return -1.f; }
+    struct I { float2 nx, ny, nz, m; };
+    struct J { float2 x, y, z, m; };
+    struct C { float2 eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.nx = dup(-pair_get(a.src, i, 0));
+        s.ny = dup(-pair_get(a.src, i, 1));
+        s.nz = dup(-pair_get(a.src, i, 2));
+        s.m = dup(pair_get(a.src, i, 3));
+    }
+    __device__ static void load_j(const float4 *rec, J &j) {
+        const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+        j.x = f2(r0.x, r0.y);
+        j.y = f2(r0.z, r0.w);
+        j.z = f2(r1.x, r1.y);
+        j.m = f2(r1.z, r1.w);
+    }
+    __device__ static void shfl(J &j, int src) {
+        j.x = shfl2(j.x, src);
+        j.y = shfl2(j.y, src);
+        j.z = shfl2(j.z, src);
+        j.m = shfl2(j.m, src);
+    }
+    template <bool MASK>
+    __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
+                                                float2 (&aj)[NACC], const C &c, float2) {
+        const float2 dx = __fadd2_rn(j.x, s.nx);
+        const float2 dy = __fadd2_rn(j.y, s.ny);
+        const float2 dz = __fadd2_rn(j.z, s.nz);
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        const float2 y = rsqrt_mufu2(q);
+        const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
+        const float2 wi = __fmul2_rn(j.m, y3);  // j on i: +m_j s^-3/2 d
+        ai[0] = __ffma2_rn(wi, dx, ai[0]);
+        ai[1] = __ffma2_rn(wi, dy, ai[1]);
+        ai[2] = __ffma2_rn(wi, dz, ai[2]);
+        const float2 wj = __fmul2_rn(s.m, y3);  // i on j: -m_i s^-3/2 d (sign at the store)
+        aj[0] = __ffma2_rn(wj, dx, aj[0]);
+        aj[1] = __ffma2_rn(wj, dy, aj[1]);
+        aj[2] = __ffma2_rn(wj, dz, aj[2]);
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const float (&f)[NACC]) {
+        const float G = (float)a.G;
+        finish_fp32(a, i, G * f[0], G * f[1], G * f[2]);
+    }
+};
+
+// Adjoint VJP: sums (U_x, U_y, U_z, V, W_x, W_y, W_z, P), records as the
+// one-sided VJP's {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,0,0}.
+struct SymVjp {
+    static constexpr int R = kSymVjpR;
+    static constexpr int NACC = 8;
+    static constexpr int REC_F4 = 4;
+    static constexpr bool SELF_MASK = true;
+    // j side: U as is; V gathered with -m_i; W and P with the sign flipped
+    __host__ __device__ static constexpr float jsign(int k) { return k < 3 ? 1.f : -1.f; }
+    struct I { float2 nx, ny, nz, nm, ax, ay, az; };  // nm = -m_i
+    struct J { float2 x, y, z, m, ax, ay, az; };
+    struct C { float2 eps2; };
+    __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.nx = dup(-vrec_get(a.src, i, 0));
+        s.ny = dup(-vrec_get(a.src, i, 1));
+        s.nz = dup(-vrec_get(a.src, i, 2));
+        s.nm = dup(-vrec_get(a.src, i, 3));
+        s.ax = dup(vrec_get(a.src, i, 4));
+        s.ay = dup(vrec_get(a.src, i, 5));
+        s.az = dup(vrec_get(a.src, i, 6));
+    }
+    __device__ static void load_j(const float4 *rec, J &j) {
+        const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
+        j.x = f2(r0.x, r0.y);
+        j.y = f2(r0.z, r0.w);
+        j.z = f2(r1.x, r1.y);
+        j.m = f2(r1.z, r1.w);
+        j.ax = f2(r2.x, r2.y);
+        j.ay = f2(r2.z, r2.w);
+        j.az = f2(r3.x, r3.y);
+    }
+    __device__ static void shfl(J &j, int src) {
+        j.x = shfl2(j.x, src);
+        j.y = shfl2(j.y, src);
+        j.z = shfl2(j.z, src);
+        j.m = shfl2(j.m, src);
+        j.ax = shfl2(j.ax, src);
+        j.ay = shfl2(j.ay, src);
+        j.az = shfl2(j.az, src);
+    }
+    template <bool MASK>
+    __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
+                                                float2 (&aj)[NACC], const C &c, float2 keep) {
+        const float2 dx = __fadd2_rn(j.x, s.nx);
+        const float2 dy = __fadd2_rn(j.y, s.ny);
+        const float2 dz = __fadd2_rn(j.z, s.nz);
+        float2 q = __ffma2_rn(dx, dx, c.eps2);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dz, dz, q);
+        float2 y = rsqrt_mufu2(q);
+        if constexpr (MASK) y = __fmul2_rn(y, keep);
+        const float2 y2 = __fmul2_rn(y, y);
+        const float2 f = __fmul2_rn(y, y2);
+        const float2 h = __fmul2_rn(f, y2);
+        float2 e = __fmul2_rn(j.ax, dx);  // abar_j . d
+        e = __ffma2_rn(j.ay, dy, e);
+        e = __ffma2_rn(j.az, dz, e);
+        float2 g = __fmul2_rn(s.ax, dx);  // abar_i . d
+        g = __ffma2_rn(s.ay, dy, g);
+        g = __ffma2_rn(s.az, dz, g);
+        const float2 hc = __fmul2_rn(h, __ffma2_rn(j.m, g, __fmul2_rn(s.nm, e)));  // h (m_j g - m_i e)
+        ai[0] = __ffma2_rn(f, j.ax, ai[0]);
+        ai[1] = __ffma2_rn(f, j.ay, ai[1]);
+        ai[2] = __ffma2_rn(f, j.az, ai[2]);
+        ai[3] = __ffma2_rn(f, j.m, ai[3]);
+        ai[4] = __ffma2_rn(hc, dx, ai[4]);
+        ai[5] = __ffma2_rn(hc, dy, ai[5]);
+        ai[6] = __ffma2_rn(hc, dz, ai[6]);
+        ai[7] = __ffma2_rn(f, e, ai[7]);
+        aj[0] = __ffma2_rn(f, s.ax, aj[0]);
+        aj[1] = __ffma2_rn(f, s.ay, aj[1]);
+        aj[2] = __ffma2_rn(f, s.az, aj[2]);
+        aj[3] = __ffma2_rn(f, s.nm, aj[3]);
+        aj[4] = __ffma2_rn(hc, dx, aj[4]);
+        aj[5] = __ffma2_rn(hc, dy, aj[5]);
+        aj[6] = __ffma2_rn(hc, dz, aj[6]);
+        aj[7] = __ffma2_rn(f, g, aj[7]);
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t k, const float (&s)[NACC]) {
+        VjpF32x2::F f;
+        f.ux = s[0]; f.uy = s[1]; f.uz = s[2]; f.v = s[3];
+        f.wx = s[4]; f.wy = s[5]; f.wz = s[6]; f.p = s[7];
+        VjpF32x2::finish(a, k, f);
+    }
+};
 
 // Item t of the upper triangle, rows bi = 0..nb-1 holding bj = bi..nb-1.
 __device__ __forceinline__ void sym_item(int t, int nb, int &bi, int &bj) {
@@ -47,10 +202,40 @@ __device__ __forceinline__ void sym_item(int t, int nb, int &bi, int &bj) {
     bj = r + (t - start(r));
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32) sym_force_kernel(const ForceArgs a) {
-    constexpr int R = kSymR, B = W * 32 * R;
-    extern __shared__ float acc_j[];  // [W][3][B]
+// The 32 rounds of one chunk. MASK: the diagonal item of a policy that
+// masks its own pair; i_off[r] and j_off are offsets within the block.
+#ifndef NB_SYM_ROUND_UNROLL
+#define NB_SYM_ROUND_UNROLL 1
+#endif
+constexpr int kRoundUnroll = NB_SYM_ROUND_UNROLL;  // rounds per unrolled step (build flag)
+
+template <class S, bool MASK>
+__device__ __forceinline__ void chunk_rounds(typename S::J &sj, const typename S::I (&si)[S::R],
+                                             float2 (&ai)[S::R][S::NACC], float2 (&aj)[S::NACC],
+                                             const typename S::C &c, int l, int next, int i_base,
+                                             int j_base) {
+#pragma unroll kRoundUnroll
+    for (int round = 0; round < 32; ++round) {
+        const int j0 = j_base + 2 * ((l + round) & 31);  // the current record's first body
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) {
+            float2 keep = f2(1.f, 1.f);
+            if constexpr (MASK) {
+                const int i = i_base + 32 * r;
+                keep = f2(i == j0 ? 0.f : 1.f, i == j0 + 1 ? 0.f : 1.f);
+            }
+            S::template pair<MASK>(sj, si[r], ai[r], aj, c, keep);
+        }
+        S::shfl(sj, next);
+#pragma unroll
+        for (int k = 0; k < S::NACC; ++k) aj[k] = shfl2(aj[k], next);
+    }
+}
+
+template <class S, int W>
+__global__ void __launch_bounds__(W * 32) sym_kernel(const ForceArgs a) {
+    constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
+    extern __shared__ float acc_j[];  // [W][NA][B]
     // the previous kernel on the stream (last step's epilogue reads P and
     // writes the records read here) must be complete
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -59,108 +244,82 @@ __global__ void __launch_bounds__(W * 32) sym_force_kernel(const ForceArgs a) {
     sym_item(blockIdx.x, nb, bi, bj);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int next = (l + 1) & 31;
-    const float2 eps2 = dup(a.eps2);
-    float2 nx[R], ny[R], nz[R], mi[R], ax[R], ay[R], az[R];
-    const int64_t gbase = (int64_t)bi * B + w * 32 * R;
+    typename S::C c;
+    S::consts(a, c);
+    typename S::I si[R];
+    float2 ai[R][NA];
+    const int i_base = w * 32 * R + l;  // offset of this lane's first i-body in block bi
+    const int64_t gbase = (int64_t)bi * B;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int64_t i = gbase + l + 32 * r;
-        nx[r] = dup(-pair_get(a.src, i, 0));
-        ny[r] = dup(-pair_get(a.src, i, 1));
-        nz[r] = dup(-pair_get(a.src, i, 2));
-        mi[r] = dup(pair_get(a.src, i, 3));
-        ax[r] = ay[r] = az[r] = f2(0.f, 0.f);
+        S::load_i(a, gbase + i_base + 32 * r, si[r]);
+#pragma unroll
+        for (int k = 0; k < NA; ++k) ai[r][k] = f2(0.f, 0.f);
     }
     const bool diag = bi == bj;
-    float *mine = acc_j + w * 3 * B;
-    for (int c = 0; c < B / 64; ++c) {
-        const int64_t q = (int64_t)bj * (B / 2) + c * 32 + l;  // this lane's record
-        const float4 r0 = __ldg(a.src + 2 * q), r1 = __ldg(a.src + 2 * q + 1);
-        float2 xj = f2(r0.x, r0.y), yj = f2(r0.z, r0.w), zj = f2(r1.x, r1.y), mj = f2(r1.z, r1.w);
-        float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
-#pragma unroll 1
-        for (int round = 0; round < 32; ++round) {
+    float *mine = acc_j + w * NA * B;
+    for (int ch = 0; ch < B / 64; ++ch) {
+        const int64_t q = (int64_t)bj * (B / 2) + ch * 32 + l;  // this lane's record
+        typename S::J sj;
+        S::load_j(a.src + q * S::REC_F4, sj);
+        float2 aj[NA];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 dx = __fadd2_rn(xj, nx[r]);
-                const float2 dy = __fadd2_rn(yj, ny[r]);
-                const float2 dz = __fadd2_rn(zj, nz[r]);
-                float2 s = __ffma2_rn(dx, dx, eps2);
-                s = __ffma2_rn(dy, dy, s);
-                s = __ffma2_rn(dz, dz, s);
-                const float2 y = rsqrt_mufu2(s);
-                const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
-                const float2 wi = __fmul2_rn(mj, y3);  // j on i: +m_j s^-3/2 d
-                ax[r] = __ffma2_rn(wi, dx, ax[r]);
-                ay[r] = __ffma2_rn(wi, dy, ay[r]);
-                az[r] = __ffma2_rn(wi, dz, az[r]);
-                const float2 wj = __fmul2_rn(mi[r], y3);  // i on j: -m_i s^-3/2 d
-                bx = __ffma2_rn(wj, dx, bx);
-                by = __ffma2_rn(wj, dy, by);
-                bz = __ffma2_rn(wj, dz, bz);
-            }
-            xj = shfl2(xj, next);
-            yj = shfl2(yj, next);
-            zj = shfl2(zj, next);
-            mj = shfl2(mj, next);
-            bx = shfl2(bx, next);
-            by = shfl2(by, next);
-            bz = shfl2(bz, next);
-        }
+        for (int k = 0; k < NA; ++k) aj[k] = f2(0.f, 0.f);
+        if (S::SELF_MASK && diag)
+            chunk_rounds<S, true>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
+        else
+            chunk_rounds<S, false>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
         if (!diag) {
-            const int k = c * 64 + 2 * l;
-            mine[k] = -bx.x;
-            mine[k + 1] = -bx.y;
-            mine[B + k] = -by.x;
-            mine[B + k + 1] = -by.y;
-            mine[2 * B + k] = -bz.x;
-            mine[2 * B + k + 1] = -bz.y;
+            const int kb = ch * 64 + 2 * l;
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                mine[k * B + kb] = S::jsign(k) * aj[k].x;
+                mine[k * B + kb + 1] = S::jsign(k) * aj[k].y;
+            }
         }
     }
     float *P = reinterpret_cast<float *>(a.part);
     const int64_t np = a.npad;
     {
-        float *p = P + (int64_t)bj * 3 * np;
+        float *p = P + (int64_t)bj * NA * np + gbase;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int64_t i = gbase + l + 32 * r;
-            __stcg(p + i, ax[r].x + ax[r].y);
-            __stcg(p + np + i, ay[r].x + ay[r].y);
-            __stcg(p + 2 * np + i, az[r].x + az[r].y);
-        }
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < NA; ++k) __stcg(p + k * np + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
     }
     if (!diag) {
         __syncthreads();
-        float *p = P + (int64_t)bi * 3 * np + (int64_t)bj * B;
+        float *p = P + (int64_t)bi * NA * np + (int64_t)bj * B;
         for (int t = threadIdx.x; t < B; t += W * 32) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int k = 0; k < NA; ++k) {
                 float s = 0.f;
 #pragma unroll
-                for (int k = 0; k < W; ++k) s += acc_j[k * 3 * B + c * B + t];
-                __stcg(p + c * np + t, s);
+                for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
+                __stcg(p + k * np + t, s);
             }
         }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Fixed-order sum of the nb partials of each body, then the shared epilogue.
+// Fixed-order sum of the nb partials of each body, then the policy's epilogue.
+template <class S>
 __global__ void __launch_bounds__(256) sym_finish_kernel(const ForceArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
         const float *P = reinterpret_cast<const float *>(a.part);
         const int64_t np = a.npad;
-        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float f[S::NACC];
+#pragma unroll
+        for (int k = 0; k < S::NACC; ++k) f[k] = 0.f;
         for (int p = 0; p < a.ntiles; ++p) {
-            const float *q = P + (int64_t)p * 3 * np + i;
-            fx += __ldcs(q);
-            fy += __ldcs(q + np);
-            fz += __ldcs(q + 2 * np);
+            const float *q = P + (int64_t)p * S::NACC * np + i;
+#pragma unroll
+            for (int k = 0; k < S::NACC; ++k) f[k] += __ldcs(q + k * np);
         }
-        const float G = (float)a.G;
-        finish_fp32(a, i, G * fx, G * fy, G * fz);
+        S::finish(a, i, f);
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -182,11 +341,16 @@ cudaError_t launch_ex(const void *fn, dim3 grid, dim3 block, size_t smem, bool p
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template <int W>
+template <class S, int W>
+constexpr size_t sym_smem() {
+    return (size_t)W * S::NACC * (W * 32 * S::R) * 4;
+}
+
+template <class S, int W>
 cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
-    constexpr int B = W * 32 * kSymR;
-    const size_t smem = (size_t)W * 3 * B * 4;
-    auto k = sym_force_kernel<W>;
+    constexpr int B = W * 32 * S::R;
+    constexpr size_t smem = sym_smem<S, W>();
+    auto k = sym_kernel<S, W>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -198,30 +362,39 @@ cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     // the epilogue is a programmatic dependent of the pair kernel: its launch
     // overlaps the pair kernel's last wave, and it waits for its completion
-    return launch_ex((const void *)sym_finish_kernel, dim3((unsigned)((a.n + 255) / 256)),
+    return launch_ex((const void *)sym_finish_kernel<S>, dim3((unsigned)((a.n + 255) / 256)),
                      dim3(256), 0, true, a, st);
 }
 
-template <int W>
+template <class S, int W>
 int occ_sym(int) {
-    constexpr int B = W * 32 * kSymR;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_force_kernel<W>, W * 32,
-                                                      (size_t)W * 3 * B * 4) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel<S, W>, W * 32, sym_smem<S, W>()) !=
+        cudaSuccess)
         return 0;
     return b;
 }
 
-const ForceEntry kTable[] = {
-    {64, kSymR, &launch_sym<2>, &occ_sym<2>},   // blocks of 512 bodies
-    {128, kSymR, &launch_sym<4>, &occ_sym<4>},  // blocks of 1024 bodies
+// Shape (nt, r) = (threads per CTA, bodies per lane); the block is nt x r.
+const ForceEntry kAccel[] = {
+    {64, SymAccel::R, &launch_sym<SymAccel, 2>, &occ_sym<SymAccel, 2>},   // blocks of 512
+    {128, SymAccel::R, &launch_sym<SymAccel, 4>, &occ_sym<SymAccel, 4>},  // blocks of 1024
+};
+const ForceEntry kVjp[] = {
+    {64, SymVjp::R, &launch_sym<SymVjp, 2>, &occ_sym<SymVjp, 2>},   // blocks of 256
+    {128, SymVjp::R, &launch_sym<SymVjp, 4>, &occ_sym<SymVjp, 4>},  // blocks of 512
 };
 
 }  // namespace
 
 const ForceEntry *table_sym(int *count) {
-    *count = (int)(sizeof(kTable) / sizeof(kTable[0]));
-    return kTable;
+    *count = (int)(sizeof(kAccel) / sizeof(kAccel[0]));
+    return kAccel;
+}
+
+const ForceEntry *table_vjp_sym(int *count) {
+    *count = (int)(sizeof(kVjp) / sizeof(kVjp[0]));
+    return kVjp;
 }
 
 }  // namespace nb

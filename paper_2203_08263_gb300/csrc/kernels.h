@@ -19,15 +19,23 @@ enum Pol : int {
     kPolDiv = 6,     // ablation: sqrt + division
     kPolPow = 7,     // ablation: powf
     kPolSym = 8,     // plain FP32 forces, each unordered pair once (csrc/k_sym.cu)
-    kPolCount = 9
+    kPolVjpSym = 9,  // adjoint VJP, FP32 state, each unordered pair once (csrc/k_sym.cu)
+    kPolCount = 10
 };
 
-// Bodies per lane of the pair-symmetric policy; its table holds blocks of
-// 32 x R x (2 or 4 warps) = 512 or 1024 bodies (Shape: nt = 64 or 128, r = R,
-// jt = the block, split = 1).
+// Bodies per lane of the pair-symmetric force policy; its table holds blocks
+// of 32 x R x (2 or 4 warps) = 512 or 1024 bodies (Shape: nt = 64 or 128,
+// r = R, jt = the block, split = 1). The VJP's holds R = 4, blocks of 256 or
+// 512 bodies.
 constexpr int kSymR = 8;
-// The pair-symmetric policy keeps one partial per body and partner block,
-// nb x 3 x npad floats; above this many bytes the one-sided policy serves.
+#ifndef NB_SYM_VJP_R
+#define NB_SYM_VJP_R 4
+#endif
+constexpr int kSymVjpR = NB_SYM_VJP_R;
+inline bool pol_is_sym(int pol) { return pol == kPolSym || pol == kPolVjpSym; }
+// sums per body of a pair-symmetric policy (its partials: nb x sums x npad floats)
+inline int sym_sums(int pol) { return pol == kPolVjpSym ? 8 : 3; }
+// Above this many bytes of partials the one-sided policy serves.
 constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
 
 struct Shape {

@@ -29,6 +29,8 @@ def main():
                     help="nb_run path for --pol step / step-comp: 0 chosen per size, 1 graph, 2 one cluster")
     ap.add_argument("--form", type=int, default=0,
                     help="FP32 force form: 0 chosen per size, 1 one-sided, 512/1024 pair-symmetric blocks")
+    ap.add_argument("--vjp-form", type=int, default=0,
+                    help="FP32 VJP form: 0 chosen per size, 1 one-sided, 256/512 pair-symmetric blocks")
     ap.add_argument("--peaks", action="store_true")
     a = ap.parse_args()
 
@@ -36,7 +38,7 @@ def main():
 
     from paper_2203_08263_gb300 import build, ics
     from paper_2203_08263_gb300.nbody import (MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, NB_DBG_FORM,
-                                              NB_DBG_RUN_PATH, Context)
+                                              NB_DBG_RUN_PATH, NB_DBG_VJP_FORM, Context)
 
     build.build()
     if a.peaks:
@@ -52,6 +54,7 @@ def main():
     ctx = Context(1.0, 0.05, 1e-3, precision=prec, tile_override=shape)
     ctx.debug_set(NB_DBG_RUN_PATH, a.path)
     ctx.debug_set(NB_DBG_FORM, a.form)
+    ctx.debug_set(NB_DBG_VJP_FORM, a.vjp_form)
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,

@@ -15,7 +15,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-FP32_FORWARD = [256, 512, 1024, 2048, 4096, 8192, 16384, 65536, 262144, 524288]
+FP32_FORWARD = [256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072, 262144, 524288]
 FP32_ADJOINT = [2048, 16384]
 COMP_FORWARD = [256, 512, 1024, 2048, 4096, 8192, 16384, 1048576]
 COMP_ADJOINT = [2048, 16384]

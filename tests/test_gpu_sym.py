@@ -1,8 +1,8 @@
-"""GPU parity of the pair-symmetric FP32 force form (each unordered pair once,
-both bodies updated with opposite signs) against the FP64 oracle, through the
-C-ABI: accelerations (<= 2e-5 relative L2), runs of both update schemes,
-checkpoints, determinism, the adjoint's recompute, and the padding of the
-step buffers."""
+"""GPU parity of the pair-symmetric FP32 kernels (each unordered pair once,
+its terms added to both bodies) against the FP64 oracle, through the C-ABI:
+accelerations (<= 2e-5 relative L2), runs of both update schemes,
+checkpoints, determinism, the adjoint VJP (<= 5e-5) and whole adjoints, and
+the padding of the step buffers."""
 import numpy as np
 import pytest
 
@@ -167,3 +167,87 @@ def test_step_buffer_padding_not_stale(nbm, form):
     xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 6)
     assert rel_l2(to_np(x), xr) <= 1e-5
     assert rel_l2(to_np(v), vr) <= 1e-4
+
+
+# ------------------------------------------------------------- adjoint VJP
+
+@pytest.mark.parametrize("block", [256, 512])
+@pytest.mark.parametrize("n", [2, 31, 64, 65, 257, 513, 2000])
+def test_sym_vjp_matches_oracle(nbm, block, n):
+    """The pair-symmetric VJP (each pair's x-bar and m-bar terms for both
+    bodies from one evaluation; the own pair masked) against the FP64 oracle,
+    at the one-sided FP32 VJP's tolerance."""
+    G, eps = 1.0, 0.01
+    s = ics.cube(n, seed=60 + n)
+    ab = np.random.default_rng(n).normal(size=(n, 3))
+    ctx = nbm.Context(G, eps, 1e-3)
+    ctx.debug_set(nbm.NB_DBG_VJP_FORM, block)
+    assert ctx.get_config(n, nbm.MODE_ADJOINT)["form"] == "vjp_pair_symmetric"
+    xb, mb = ctx.vjp(_t(s.x), _t(s.m), _t(ab))
+    rx, rm = oracle.vjp(s.x, s.m, G, eps, ab)
+    assert rel_l2(to_np(xb), rx) <= 5e-5 and rel_l2(to_np(mb), rm) <= 5e-5
+
+
+def test_sym_vjp_plummer_and_determinism(nbm):
+    n, G, eps = 9000, 1.0, 0.05
+    s = ics.plummer(n, seed=6)
+    ab = np.random.default_rng(2).normal(size=(n, 3))
+    ctx = nbm.Context(G, eps, 1e-3)
+    ctx.debug_set(nbm.NB_DBG_VJP_FORM, 512)
+    xb1, mb1 = ctx.vjp(_t(s.x), _t(s.m), _t(ab))
+    xb2, mb2 = ctx.vjp(_t(s.x), _t(s.m), _t(ab))
+    ctx.sync()
+    assert torch.equal(xb1, xb2) and torch.equal(mb1, mb2)
+    rx, rm = oracle.vjp(s.x, s.m, G, eps, ab)
+    assert rel_l2(to_np(xb1), rx) <= 5e-5 and rel_l2(to_np(mb1), rm) <= 5e-5
+
+
+@pytest.mark.parametrize("vjp_block", [256, 512])
+def test_sym_adjoint_vs_fp64_oracle(nbm, vjp_block):
+    """nb_adjoint with pair-symmetric forward recompute and VJP (N=64, T=20,
+    the adjoint check size): the FP32 gradient against the FP64 oracle's,
+    at the one-sided FP32 adjoint's bound."""
+    n, T, k = 64, 20, 5
+    s = ics.cube(n, seed=4, masses="equal")
+    xstar = ics.targets(n, seed=4)
+    G, eps, dt = 1.0, 0.01, 1e-3
+    ctx = nbm.Context(G, eps, dt)
+    ctx.debug_set(nbm.NB_DBG_FORM, 512)
+    ctx.debug_set(nbm.NB_DBG_VJP_FORM, vjp_block)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    ck = torch.empty((T // k + 1, n, 6), dtype=torch.float32, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - _t(xstar))
+    got = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    ref = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    errs = [rel_l2(to_np(g), r) for g, r in zip(got, ref)]
+    assert max(errs) <= 1e-3, errs
+
+
+def test_sym_adjoint_midsize_matches_one_sided(nbm):
+    """N = 3000, T = 24, k = 8: gradients with both pair-symmetric kernels
+    against the all-one-sided run and the FP64 oracle."""
+    n, T, k = 3000, 24, 8
+    s = ics.cube(n, seed=14, masses="equal")
+    xstar = ics.targets(n, seed=14)
+    G, eps, dt = 1.0, 0.01, 1e-3
+    grads = {}
+    for form, vform in ((1, 1), (1024, 512)):
+        ctx = nbm.Context(G, eps, dt)
+        ctx.debug_set(nbm.NB_DBG_FORM, form)
+        ctx.debug_set(nbm.NB_DBG_VJP_FORM, vform)
+        ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+        x, v, m = _t(s.x), _t(s.v), _t(s.m)
+        ck = torch.empty((T // k + 1, n, 6), dtype=torch.float32, device=DEV)
+        ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+        xbT = 2 * (x - _t(xstar))
+        g = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+        ctx.sync()
+        grads[form] = [to_np(t) for t in g]
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    ref = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    for a, b, r in zip(grads[1024], grads[1], ref):
+        assert rel_l2(a, b) <= 1e-4
+        assert rel_l2(a, r) <= 1e-3
