@@ -179,6 +179,7 @@ def run_reference(args):
 # of block-pair partials (0.8 GB at N = 262144); its entry is scaled from a
 # capture at N = 131072 by (262144 / 131072)^2 (the partials grow as N^2).
 STEP_TRAFFIC_BYTES = {
+    (128, 8, 1, 1024): (2.14e6 + 140.18e6) * 4,
     (128, 8, 19, 128): 11.85e6 + 34.15e6,
     (128, 8, 19, 64): 11.07e6 + 34.31e6,
     (128, 4, 16, 256): 11.16e6 + 21.29e6,
