@@ -111,17 +111,19 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  * float64). Inputs are read-only.
  *
  * Force forms (the same sum in every form; nb_get_form tells which one
- * serves a size): in FP32 a one-sided kernel sums over j for every i; from
+ * serves a size). A one-sided kernel sums over j for every i. From
  * n = 32768 up (or where nb_autotune finds it faster) a pair-symmetric
  * kernel evaluates each unordered pair {i, j} once and adds its term to both
  * bodies with opposite signs (Newton's third law), into per-block partials
- * that a second kernel adds in a fixed order. It keeps nb x 3 x npad floats
- * of partials in the context (nb = npad / 1024 blocks of 1024 bodies,
- * npad = n rounded up to a block: about 12 n^2 / 1024 bytes, 0.8 GB at
- * n = 262144); systems whose partials would exceed 8 GiB use the one-sided
- * kernel. The FP32 VJP of nb_vjp and nb_adjoint has the same two forms (the
- * pair-symmetric one from n = 8192, blocks of 256 or 512 bodies, 8 sums per
- * body: about 32 n^2 / 256 bytes of partials at n < 65536). Results are
+ * that a second kernel adds in a fixed order: in FP32, and in the precision
+ * form with FP32 pair terms and the partials two-summed before the FP64
+ * update. It keeps nb x 3 x npad floats of partials in the context
+ * (nb = npad / B blocks of B = 512 or 1024 bodies, npad = n rounded up to a
+ * block: about 12 n^2 / 1024 bytes, 0.8 GB at n = 262144, 12 GiB at
+ * n = 2^20). The FP32 VJP of nb_vjp and nb_adjoint has the same two forms
+ * (the pair-symmetric one from n = 8192, blocks of 256 or 512 bodies,
+ * 8 sums per body: about 32 n^2 / 256 bytes at n < 65536). Systems whose
+ * partials would exceed 16 GiB use the one-sided kernels. Results are
  * deterministic in every form.
  */
 nb_status nb_accel(nb_ctx *ctx, int64_t n, const void *x, const void *m, void *a,
@@ -256,7 +258,8 @@ typedef enum {
     NB_FORM_SQRT_DIV = 6,        /* ablation: sqrt then division */
     NB_FORM_POW = 7,             /* ablation: powf */
     NB_FORM_PAIR_SYMMETRIC = 8,  /* FP32, each unordered pair once */
-    NB_FORM_VJP_PAIR_SYMMETRIC = 9 /* adjoint VJP, FP32, each unordered pair once */
+    NB_FORM_VJP_PAIR_SYMMETRIC = 9, /* adjoint VJP, FP32, each unordered pair once */
+    NB_FORM_COMPENSATED_PAIR_SYMMETRIC = 10 /* compensated, FP64 state, each pair once */
 } nb_form;
 
 /* The force-sum form (nb_form) the context would use for (n, mode), mode as
@@ -299,10 +302,11 @@ typedef enum {
      * launches, 2 = one-cluster kernel, 3 = its grid form
      * (NB_ERR_UNSUPPORTED at nb_run when the system does not qualify). */
     NB_DBG_RUN_PATH = 4,
-    /* FP32 forward force form: 0 = chosen per size (default), 1 = one-sided
-     * kernels only, 512 or 1024 = the pair-symmetric kernel with blocks of
-     * that many bodies at every size (nb_run's graph path; the fused
-     * small-system paths keep their own kernel). */
+    /* Forward force form (FP32 and the precision form): 0 = chosen per size
+     * (default), 1 = one-sided kernels only, 512 or 1024 = the
+     * pair-symmetric kernel with blocks of that many bodies at every size
+     * (nb_run's graph path; the fused small-system paths keep their own
+     * kernel). */
     NB_DBG_FORM = 5,
     /* FP32 VJP form (nb_vjp, nb_adjoint): 0 = chosen per size (default),
      * 1 = one-sided only, 256 or 512 = the pair-symmetric kernel with blocks

@@ -21,7 +21,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     NB_CUDA(cudaSetDevice(ctx->device));
     std::vector<int> pols;
     if (mode == 0) {
-        if (f64_state(ctx)) pols = {kPolComp};
+        if (f64_state(ctx)) pols = n >= 8192 ? std::vector<int>{kPolComp, kPolSymComp} : std::vector<int>{kPolComp};
         else if (ctx->math == 0 && n >= 8192) pols = {kPolF32x2, kPolScalar, kPolSym};
         else pols = {kPolF32x2, kPolScalar};
     } else if (f64_state(ctx)) {
@@ -44,7 +44,13 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
     cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     auto time_shape = [&](const Shape &s, float *ms) -> nb_status {
         Plan p;
-        NB_TRY(make_plan(ctx, s, n, &p));
+        const nb_status ps = make_plan(ctx, s, n, &p);
+        if (ps == NB_ERR_UNSUPPORTED && pol_is_sym(s.pol)) {  // partials above the cap: not a candidate
+            ctx->err.clear();
+            *ms = 1e30f;
+            return NB_OK;
+        }
+        NB_TRY(ps);
         const size_t cap = pol_is_sym(s.pol) ? kSymMaxPartBytes : ((size_t)1 << 31);
         if (p.part_bytes > cap) { *ms = 1e30f; return NB_OK; }
         NB_TRY(plan_scratch(ctx, p));

@@ -20,6 +20,7 @@ const ForceEntry *table_div(int *count);
 const ForceEntry *table_pow(int *count);
 const ForceEntry *table_sym(int *count);
 const ForceEntry *table_vjp_sym(int *count);
+const ForceEntry *table_comp_sym(int *count);
 
 const ForceEntry *force_table(int pol, int *count) {
     switch (pol) {
@@ -33,6 +34,7 @@ const ForceEntry *force_table(int pol, int *count) {
         case kPolPow: return table_pow(count);
         case kPolSym: return table_sym(count);
         case kPolVjpSym: return table_vjp_sym(count);
+        case kPolSymComp: return table_comp_sym(count);
         default: *count = 0; return nullptr;
     }
 }
@@ -190,14 +192,14 @@ Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_
 Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     const int pol = mode_pol(ctx, mode);
     int nt = 128, r = 1, jt = 64;
-    if (pol == kPolF32x2 && allow_sym && n >= 32768) {
+    if ((pol == kPolF32x2 || pol == kPolComp) && allow_sym && n >= 32768) {
         // each unordered pair once, blocks of 1024 bodies from 2^17 up (enough
         // block pairs to fill the GPU), 512 below; the one-sided policy above
         // the partial-buffer cap
         const int snt = n >= 131072 ? 128 : 64;
         const int64_t b = (int64_t)snt * kSymR, np = round_up(n, b);
         if ((size_t)(np / b) * 3 * (size_t)np * 4 <= kSymMaxPartBytes)
-            return Shape{kPolSym, snt, kSymR, 1, (int)b};
+            return Shape{pol == kPolComp ? kPolSymComp : kPolSym, snt, kSymR, 1, (int)b};
     }
     if (pol == kPolF32x2) {
         if (n >= 32768) { r = 4; jt = 128; }
@@ -242,8 +244,9 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
         *out = s;
         return NB_OK;
     }
-    if (pol == kPolF32x2 && ctx->form_pin > 1) {
-        *out = Shape{kPolSym, ctx->form_pin / kSymR, kSymR, 1, ctx->form_pin};
+    if ((pol == kPolF32x2 || pol == kPolComp) && ctx->form_pin > 1) {
+        *out = Shape{pol == kPolComp ? kPolSymComp : kPolSym, ctx->form_pin / kSymR, kSymR, 1,
+                     ctx->form_pin};
         return NB_OK;
     }
     if (pol == kPolVjp && ctx->vjp_form_pin > 1) {

@@ -17,6 +17,11 @@
 // 2 x 26 one-sided. The VJP's own pair (j == i) is masked: its f = eps^-3
 // terms cancel only in the epilogue's FP32 sums.
 //
+// Precision form (FP64 state, Section 2.3's sum with compensated
+// accumulation): the force pair terms in FP32, FP32 sums within a block pair,
+// and the block-pair partials two-summed in the epilogue before the FP64
+// update.
+//
 // Work decomposition. Bodies are padded with zero-mass bodies to nb blocks of
 // B = 32 x W x R. An item is a block pair (bi, bj), bi <= bj, one CTA each.
 // Each warp of the CTA owns 32 x R bodies of block bi, R per lane, held
@@ -96,9 +101,45 @@ struct SymAccel {
         aj[1] = __ffma2_rn(wj, dy, aj[1]);
         aj[2] = __ffma2_rn(wj, dz, aj[2]);
     }
-    __device__ static void finish(const ForceArgs &a, int64_t i, const float (&f)[NACC]) {
+    // across partials: plain FP32 sums in block order
+    struct Fin { float s[NACC]; };
+    __device__ static void fin_zero(Fin &f) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) f.s[k] = 0.f;
+    }
+    __device__ static void fin_add(Fin &f, const float (&v)[NACC]) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) f.s[k] += v[k];
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const Fin &f) {
         const float G = (float)a.G;
-        finish_fp32(a, i, G * f[0], G * f[1], G * f[2]);
+        finish_fp32(a, i, G * f.s[0], G * f.s[1], G * f.s[2]);
+    }
+};
+
+// Precision form (FP64 state): the pair terms of SymAccel from the FP32
+// packed positions; each block-pair partial is an FP32 sum, and the epilogue
+// two-sums the partials in block order into (hi, lo) per component (about
+// 2^-44 relative), widens once and runs the FP64 update, as the one-sided
+// compensated policy does with its tile sums.
+struct SymComp : SymAccel {
+    struct Fin { float h[NACC], l[NACC]; };
+    __device__ static void fin_zero(Fin &f) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) f.h[k] = f.l[k] = 0.f;
+    }
+    __device__ static void fin_add(Fin &f, const float (&v)[NACC]) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) {
+            float s, e;
+            two_sum(f.h[k], v[k], s, e);
+            f.h[k] = s;
+            f.l[k] = __fadd_rn(f.l[k], e);
+        }
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t i, const Fin &f) {
+        finish_fp64(a, i, a.G * ((double)f.h[0] + (double)f.l[0]), a.G * ((double)f.h[1] + (double)f.l[1]),
+                    a.G * ((double)f.h[2] + (double)f.l[2]));
     }
 };
 
@@ -181,7 +222,17 @@ struct SymVjp {
         aj[6] = __ffma2_rn(hc, dz, aj[6]);
         aj[7] = __ffma2_rn(f, g, aj[7]);
     }
-    __device__ static void finish(const ForceArgs &a, int64_t k, const float (&s)[NACC]) {
+    struct Fin { float s[NACC]; };
+    __device__ static void fin_zero(Fin &f) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) f.s[k] = 0.f;
+    }
+    __device__ static void fin_add(Fin &f, const float (&v)[NACC]) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) f.s[k] += v[k];
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t k, const Fin &fin) {
+        const float *s = fin.s;
         VjpF32x2::F f;
         f.ux = s[0]; f.uy = s[1]; f.uz = s[2]; f.v = s[3];
         f.wx = s[4]; f.wy = s[5]; f.wz = s[6]; f.p = s[7];
@@ -303,7 +354,8 @@ __global__ void __launch_bounds__(W * 32) sym_kernel(const ForceArgs a) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Fixed-order sum of the nb partials of each body, then the policy's epilogue.
+// Sum of the nb partials of each body in block order (the policy's Fin:
+// plain FP32, or two-sums in the precision form), then the policy's epilogue.
 template <class S>
 __global__ void __launch_bounds__(256) sym_finish_kernel(const ForceArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -311,13 +363,14 @@ __global__ void __launch_bounds__(256) sym_finish_kernel(const ForceArgs a) {
     if (i < a.n) {
         const float *P = reinterpret_cast<const float *>(a.part);
         const int64_t np = a.npad;
-        float f[S::NACC];
-#pragma unroll
-        for (int k = 0; k < S::NACC; ++k) f[k] = 0.f;
+        typename S::Fin f;
+        S::fin_zero(f);
         for (int p = 0; p < a.ntiles; ++p) {
             const float *q = P + (int64_t)p * S::NACC * np + i;
+            float v[S::NACC];
 #pragma unroll
-            for (int k = 0; k < S::NACC; ++k) f[k] += __ldcs(q + k * np);
+            for (int k = 0; k < S::NACC; ++k) v[k] = __ldcs(q + k * np);
+            S::fin_add(f, v);
         }
         S::finish(a, i, f);
     }
@@ -380,6 +433,10 @@ const ForceEntry kAccel[] = {
     {64, SymAccel::R, &launch_sym<SymAccel, 2>, &occ_sym<SymAccel, 2>},   // blocks of 512
     {128, SymAccel::R, &launch_sym<SymAccel, 4>, &occ_sym<SymAccel, 4>},  // blocks of 1024
 };
+const ForceEntry kComp[] = {
+    {64, SymComp::R, &launch_sym<SymComp, 2>, &occ_sym<SymComp, 2>},   // blocks of 512
+    {128, SymComp::R, &launch_sym<SymComp, 4>, &occ_sym<SymComp, 4>},  // blocks of 1024
+};
 const ForceEntry kVjp[] = {
     {64, SymVjp::R, &launch_sym<SymVjp, 2>, &occ_sym<SymVjp, 2>},   // blocks of 256
     {128, SymVjp::R, &launch_sym<SymVjp, 4>, &occ_sym<SymVjp, 4>},  // blocks of 512
@@ -390,6 +447,11 @@ const ForceEntry kVjp[] = {
 const ForceEntry *table_sym(int *count) {
     *count = (int)(sizeof(kAccel) / sizeof(kAccel[0]));
     return kAccel;
+}
+
+const ForceEntry *table_comp_sym(int *count) {
+    *count = (int)(sizeof(kComp) / sizeof(kComp[0]));
+    return kComp;
 }
 
 const ForceEntry *table_vjp_sym(int *count) {

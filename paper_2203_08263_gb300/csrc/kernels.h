@@ -20,7 +20,8 @@ enum Pol : int {
     kPolPow = 7,     // ablation: powf
     kPolSym = 8,     // plain FP32 forces, each unordered pair once (csrc/k_sym.cu)
     kPolVjpSym = 9,  // adjoint VJP, FP32 state, each unordered pair once (csrc/k_sym.cu)
-    kPolCount = 10
+    kPolSymComp = 10,  // compensated forces, FP64 state, each unordered pair once (csrc/k_sym.cu)
+    kPolCount = 11
 };
 
 // Bodies per lane of the pair-symmetric force policy; its table holds blocks
@@ -32,11 +33,11 @@ constexpr int kSymR = 8;
 #define NB_SYM_VJP_R 4
 #endif
 constexpr int kSymVjpR = NB_SYM_VJP_R;
-inline bool pol_is_sym(int pol) { return pol == kPolSym || pol == kPolVjpSym; }
+inline bool pol_is_sym(int pol) { return pol == kPolSym || pol == kPolVjpSym || pol == kPolSymComp; }
 // sums per body of a pair-symmetric policy (its partials: nb x sums x npad floats)
 inline int sym_sums(int pol) { return pol == kPolVjpSym ? 8 : 3; }
 // Above this many bytes of partials the one-sided policy serves.
-constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
+constexpr size_t kSymMaxPartBytes = (size_t)16 << 30;
 
 struct Shape {
     int pol, nt, r, split, jt;

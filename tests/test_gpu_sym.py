@@ -111,18 +111,23 @@ def test_sym_is_deterministic(nbm):
 
 
 def test_default_form_by_size(nbm):
-    """Untuned FP32 forward: one-sided below 32768 bodies, pair-symmetric
-    from there; the precision form and the pinned one-sided form never take
-    it."""
+    """Untuned forward, both precisions: one-sided below 32768 bodies,
+    pair-symmetric from there, one-sided when pinned; the VJP from 8192."""
     ctx = nbm.Context(1.0, 0.01, 1e-3)
     if ctx.get_config(40000)["tuned"]:
         pytest.skip("a tuning table is loaded")
     assert ctx.get_config(20000)["form"] == "f32x2"
     assert ctx.get_config(40000)["form"] == "pair_symmetric"
+    assert ctx.get_config(4000, nbm.MODE_ADJOINT)["form"] == "vjp"
+    assert ctx.get_config(9000, nbm.MODE_ADJOINT)["form"] == "vjp_pair_symmetric"
     ctx.debug_set(nbm.NB_DBG_FORM, 1)
     assert ctx.get_config(40000)["form"] == "f32x2"
     comp = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
+    assert comp.get_config(20000)["form"] == "compensated"
+    assert comp.get_config(40000)["form"] == "compensated_pair_symmetric"
+    comp.debug_set(nbm.NB_DBG_FORM, 1)
     assert comp.get_config(40000)["form"] == "compensated"
+    assert comp.get_config(40000, nbm.MODE_ADJOINT)["form"] == "vjp_compensated"
 
 
 def test_sym_adjoint_matches_one_sided(nbm):
@@ -251,3 +256,34 @@ def test_sym_adjoint_midsize_matches_one_sided(nbm):
     for a, b, r in zip(grads[1024], grads[1], ref):
         assert rel_l2(a, b) <= 1e-4
         assert rel_l2(a, r) <= 1e-3
+
+
+# ----------------------------------------------------- precision form
+
+@pytest.mark.parametrize("block", [512, 1024])
+@pytest.mark.parametrize("n", [2, 33, 1000, 4097, 20000])
+def test_sym_compensated_accel_matches_oracle(nbm, block, n):
+    """FP64 state, FP32 pair terms each evaluated once for both bodies, the
+    block-pair partials two-summed: the precision form's 1e-6 bound."""
+    G, eps = 1.0, 0.05
+    s = ics.plummer(n, seed=40 + n)
+    ctx = nbm.Context(G, eps, 5e-4, precision="comp")
+    ctx.debug_set(nbm.NB_DBG_FORM, block)
+    assert ctx.get_config(n)["form"] == "compensated_pair_symmetric"
+    a = to_np(ctx.accel(_t(s.x, torch.float64), _t(s.m, torch.float64)))
+    assert rel_l2(a, oracle.accel(s.x, s.m, G, eps)) <= 1e-6
+
+
+@pytest.mark.parametrize("scheme", ["paper", "kdk"])
+def test_sym_compensated_run_matches_oracle(nbm, scheme):
+    n, G, eps, dt, T = 3000, 1.0, 0.05, 5e-4, 10
+    s = ics.plummer(n, seed=2)
+    ctx = nbm.Context(G, eps, dt, precision="comp", scheme=scheme)
+    ctx.debug_set(nbm.NB_DBG_FORM, 512)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+    f = torch.float64
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ctx.run(x, v, m, T)
+    xr, vr = oracle.run(s.x, s.v, s.m, G, eps, dt, T, scheme=scheme)
+    assert rel_l2(to_np(x), xr) <= 1e-9
+    assert rel_l2(to_np(v), vr) <= 1e-6
