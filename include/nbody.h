@@ -159,10 +159,20 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * nb_batched_max_n(); steps at most 2^20 per call. Either precision and
  * either update scheme (params.precision, params.scheme), as nb_run; the
  * precision form runs items of at most 4 bodies per thread.
- * Inside the launch, work items (system, step, chunk of T x R i-bodies for
- * T threads per CTA; R = 8, 4, 2 or 1 per item: full chunks at the shape's
- * largest R, a system's ragged rest in smaller ones) are taken from one
- * queue; a step of a system starts when its previous step is done.
+ * Inside the launch, work items are taken from one queue; a step of a
+ * system starts when its previous step is done. Two forms (nb_get_batched_form):
+ * one-sided items (system, step, chunk of T x R i-bodies for T threads per
+ * CTA against all of the system's bodies; R = 8, 4, 2 or 1 per item: full
+ * chunks at the shape's largest R, a system's ragged rest in smaller ones),
+ * or pair-symmetric items: each system in groups of 256 bodies (zero-mass
+ * padding), one item per pair of groups (each unordered pair of bodies
+ * evaluated once for both), and one epilogue item per group that adds its
+ * partials in group order and runs the update; a warp runs one item. In
+ * FP32 the pair-symmetric form is the default when its work, padding
+ * included, is below 0.85 of the one-sided form's (ensembles of systems of a
+ * few hundred bodies and more), and nb_autotune_batched times both; the
+ * precision form runs it only when pinned (its FP32 partials are longer
+ * sums than the one-sided tiles').
  */
 nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
                          const void *m, int steps, void *stream);
@@ -181,7 +191,9 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets);
 /* The batched launch the context would use for these sizes: out[0..5] =
  * {threads per CTA, largest bodies per thread of an item, j-tile bodies, work
  * items per step, CTAs in the persistent grid, origin of the shape: 0 the
- * default, 1 nb_autotune_batched, 2 nb_set_batched_config}. */
+ * default, 1 nb_autotune_batched, 2 nb_set_batched_config or
+ * nb_set_batched_form}. In the pair-symmetric form: {128, 8 bodies per lane,
+ * 256 bodies per group, items per step, CTAs, origin}. */
 nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int *out6);
 
 /*
@@ -196,6 +208,15 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
  */
 nb_status nb_set_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, int threads,
                                 int bodies_per_thread, int jtile);
+
+/* Force form of nb_run_batched for this size profile: 1 = one-sided items
+ * (with a one-sided shape pinned or tuned before, else the default shape),
+ * 2 = pair-symmetric items, 0 = remove a pinned or tuned choice (back to the
+ * default). nb_set_batched_config pins the one-sided form. */
+nb_status nb_set_batched_form(nb_ctx *ctx, int nsys, const int64_t *offsets, int form);
+/* The form nb_run_batched would use for these sizes: *form = 1 one-sided,
+ * 2 pair-symmetric. */
+nb_status nb_get_batched_form(nb_ctx *ctx, int nsys, const int64_t *offsets, int *form);
 
 /*
  * Reverse mode of nb_run with the paper scheme. Given the checkpoints written

@@ -13,6 +13,32 @@
 using namespace nb;
 using namespace nb::detail;
 
+namespace {
+
+// The plan's preset fields for these sizes: the tuned or pinned entry, else
+// the default shape, in FP32 in the pair-symmetric form when it needs less
+// than 0.85 of the one-sided form's FP32 work (groups of 256 bodies waste
+// little on systems of a few hundred bodies and more). The precision form
+// keeps the one-sided items unless pinned: the pair-symmetric items sum up to
+// 256 terms per FP32 partial against the one-sided tiles' 32 to 128, which
+// shows on close encounters (cube, eps = 0.01: positions after 4 steps
+// 4.4e-9 from the FP64 oracle against below 1e-9).
+void preset_plan(nb_ctx *ctx, const std::vector<int64_t> &off, BatchPlan &plan) {
+    plan.f64 = f64_state(ctx) ? 1 : 0;
+    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
+    if (tuned != ctx->batched_tuned.end()) {
+        plan.nt = tuned->second.nt;
+        plan.r = tuned->second.r;
+        plan.jt = tuned->second.jt;
+        plan.origin = tuned->second.origin;
+        plan.sym = tuned->second.sym;
+        return;
+    }
+    plan.sym = !plan.f64 && batched_sym_work_ratio(off) < 0.85 ? 1 : 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 int64_t nb_batched_max_n(void) { return batched_max_n(); }
@@ -35,13 +61,7 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     NB_TRY(check_ptr(ctx, m, es, "m", nullptr));
     cudaStream_t st = as_stream(stream);
     BatchPlan plan;
-    plan.f64 = f64_state(ctx) ? 1 : 0;
-    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
-    if (tuned != ctx->batched_tuned.end()) {
-        plan.nt = tuned->second.nt;
-        plan.r = tuned->second.r;
-        plan.jt = tuned->second.jt;
-    }
+    preset_plan(ctx, off, plan);
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
         return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
@@ -96,16 +116,20 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     const int probe_steps = 4;
     float best_ms = 1e30f;
     BatchPlan best;
-    static const int kShapes[][2] = {{128, 1}, {128, 2}, {128, 4}, {128, 8}, {256, 1},
-                                     {256, 2}, {256, 4}, {256, 8}, {512, 1}, {512, 2}};
+    // (threads, largest R) of the one-sided form at two j-tiles, then the
+    // pair-symmetric form (shape {0, 0}: its own)
+    static const int kShapes[][2] = {{128, 1}, {128, 2}, {128, 4}, {128, 8}, {256, 1}, {256, 2},
+                                     {256, 4}, {256, 8}, {512, 1}, {512, 2}, {0, 0}};
     for (const auto &shape : kShapes) {
         for (int jt : {64, 128}) {
             if (f64_state(ctx) && shape[1] > 4) continue;  // the precision form: R <= 4
+            if (shape[0] == 0 && (jt != 64 || f64_state(ctx))) continue;  // FP32 only (see preset_plan)
             BatchPlan plan;
             plan.f64 = f64_state(ctx) ? 1 : 0;
             plan.nt = shape[0];
             plan.r = shape[1];
             plan.jt = jt;
+            plan.sym = shape[0] == 0 ? 1 : 0;
             std::string why;
             if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why)) continue;
             NB_TRY(ensure(ctx, ctx->bat, plan.scratch_bytes, false));
@@ -144,14 +168,7 @@ nb_status nb_get_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     std::vector<int64_t> off;
     NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
     BatchPlan plan;
-    plan.f64 = f64_state(ctx) ? 1 : 0;
-    auto tuned = ctx->batched_tuned.find(sizes_signature(off));
-    if (tuned != ctx->batched_tuned.end()) {
-        plan.nt = tuned->second.nt;
-        plan.r = tuned->second.r;
-        plan.jt = tuned->second.jt;
-        plan.origin = tuned->second.origin;
-    }
+    preset_plan(ctx, off, plan);
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
         return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
@@ -193,12 +210,55 @@ nb_status nb_set_batched_config(nb_ctx *ctx, int nsys, const int64_t *offsets, i
     plan.nt = threads;
     plan.r = bodies_per_thread;
     plan.jt = jtile;
+    plan.sym = 0;
     std::string why;
     if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
         return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
     plan.origin = 2;
     ctx->batched_tuned[sig] = plan;
     clear_graphs(ctx);
+    return NB_OK;
+}
+
+nb_status nb_set_batched_form(nb_ctx *ctx, int nsys, const int64_t *offsets, int form) {
+    if (!ctx) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    if (form < 0 || form > 2) return fail(ctx, NB_ERR_INVALID, "form must be 0, 1 or 2");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    const uint64_t sig = sizes_signature(off);
+    clear_graphs(ctx);
+    if (form == 0) {
+        ctx->batched_tuned.erase(sig);
+        return NB_OK;
+    }
+    BatchPlan plan;
+    plan.f64 = f64_state(ctx) ? 1 : 0;
+    auto it = ctx->batched_tuned.find(sig);
+    if (form == 1 && it != ctx->batched_tuned.end() && !it->second.sym) {  // keep a one-sided shape
+        plan.nt = it->second.nt;
+        plan.r = it->second.r;
+        plan.jt = it->second.jt;
+    }
+    plan.sym = form == 2 ? 1 : 0;
+    std::string why;
+    if (!batched_plan(ctx->device, ctx->num_sms, off, plan, why))
+        return fail(ctx, NB_ERR_CUDA, "batched plan: %s", why.c_str());
+    plan.origin = 2;
+    ctx->batched_tuned[sig] = plan;
+    return NB_OK;
+}
+
+nb_status nb_get_batched_form(nb_ctx *ctx, int nsys, const int64_t *offsets, int *form) {
+    if (!ctx || !form) return NB_ERR_INVALID;
+    if (nsys <= 0 || !offsets) return fail(ctx, NB_ERR_INVALID, "nsys must be > 0, offsets non-NULL");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> off;
+    NB_TRY(read_offsets(ctx, nsys, offsets, ctx->side, off));
+    BatchPlan plan;
+    preset_plan(ctx, off, plan);
+    *form = plan.sym ? 2 : 1;
     return NB_OK;
 }
 

@@ -497,6 +497,7 @@ int64_t batched_max_n() { return int64_t(1) << 20; }
 bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, BatchPlan &p,
                   std::string &why) {
     (void)device;
+    if (p.sym) return batched_sym_plan(num_sms, off, p, why);
     p.nsys = (int)off.size() - 1;
     if (p.nt == 0) p.nt = 256;  // one CTA per SM: no co-resident CTA starves another
     if (p.r == 0) p.r = p.f64 ? 4 : 8;
@@ -580,6 +581,7 @@ bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, Batc
 }
 
 cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
+    if (p.sym) return batched_sym_upload(p, scratch, st);
     Layout L = layout_of(p);
     char *b = (char *)scratch;
     cudaError_t e;
@@ -601,8 +603,8 @@ cudaError_t batched_upload(const BatchPlan &p, void *scratch, cudaStream_t st) {
 
 cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, void *x, void *v, void *m,
                                    cudaStream_t st) {
-    Layout L = layout_of(p);
-    const int64_t *off = (const int64_t *)((char *)scratch + L.o_off);
+    const int64_t *off = p.sym ? batched_sym_offsets(p, scratch)
+                               : (const int64_t *)((char *)scratch + layout_of(p).o_off);
     if (p.f64)
         batched_fill_kernel<double><<<p.nsys, 256, 0, st>>>(off, (double *)x, (double *)v, (double *)m);
     else
@@ -613,6 +615,7 @@ cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, void *x, v
 cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, void *x, void *v, const void *m,
                             int steps, int kdk, float eps2, double G, double dt, int *err,
                             uint64_t timeout_ns, cudaStream_t st) {
+    if (p.sym) return batched_sym_enqueue(p, scratch, x, v, m, steps, kdk, eps2, G, dt, err, timeout_ns, st);
     if ((uint64_t)p.items_per_step * (uint64_t)(steps + 1) + (uint64_t)p.ncta * (kHold + 1) >= (1ull << 32))
         return cudaErrorInvalidValue;
     Layout L = layout_of(p);

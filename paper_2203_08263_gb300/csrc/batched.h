@@ -31,12 +31,31 @@ struct BatchPlan {
     size_t scratch_bytes = 0;   // plan + counters + two packed buffers
     uint64_t signature = 0;     // hash of sizes and shape
     int64_t launches = 3;       // memset, pack, persistent kernel
+    // The pair-symmetric form (csrc/batched_sym.cu): groups of 256 bodies,
+    // block-pair items and one epilogue item per group (nt = 128, r = 8,
+    // jt = the group; the plan fields above keep their meaning).
+    int sym = 0;
+    std::vector<int64_t> sym_pofs;         // per system: offset of its partials (floats)
+    std::vector<int> sym_ng, sym_npairs;   // per system: groups, pair items per step
+    std::vector<int> sym_items;            // per item of one step: {system, gi, gj, kind}
+    int64_t sym_part_floats = 0;
 };
 
 int64_t batched_max_n();
 
+// FP32 lane operations of the pair-symmetric form over those of the one-sided
+// form for these system sizes (the padding to whole groups included).
+double batched_sym_work_ratio(const std::vector<int64_t> &off);
+bool batched_sym_plan(int num_sms, const std::vector<int64_t> &off, BatchPlan &plan, std::string &why);
+cudaError_t batched_sym_upload(const BatchPlan &plan, void *scratch, cudaStream_t st);
+const int64_t *batched_sym_offsets(const BatchPlan &plan, void *scratch);
+cudaError_t batched_sym_enqueue(const BatchPlan &plan, void *scratch, void *x, void *v,
+                                const void *m, int steps, int kdk, float eps2, double G, double dt,
+                                int *err, uint64_t timeout_ns, cudaStream_t st);
+
 // Build the plan for the given offsets on this device. Shape fields of
-// `plan` (nt, r, jt) may be preset.
+// `plan` (nt, r, jt) may be preset; plan.sym = 1 builds the pair-symmetric
+// form (and the functions below dispatch on it).
 bool batched_plan(int device, int num_sms, const std::vector<int64_t> &off, BatchPlan &plan,
                   std::string &why);
 

@@ -53,6 +53,8 @@ SIGNATURES = {
     "nb_autotune_batched": (_i, [_vp, _i, _vp]),
     "nb_get_batched_config": (_i, [_vp, _i, _vp, _c.POINTER(_i)]),
     "nb_set_batched_config": (_i, [_vp, _i, _vp, _i, _i, _i]),
+    "nb_set_batched_form": (_i, [_vp, _i, _vp, _i]),
+    "nb_get_batched_form": (_i, [_vp, _i, _vp, _c.POINTER(_i)]),
     "nb_get_run_path": (_i, [_vp, _i64, _c.POINTER(_i)]),
     "nb_adjoint": (_i, [_vp, _i64, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nb_vjp": (_i, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -209,8 +211,18 @@ class Context:
         out = (_i * 6)()
         self._check(self.lib.nb_get_batched_config(self.h, int(offsets.shape[0]) - 1, _ptr(offsets), out),
                     "nb_get_batched_config")
+        form = _i()
+        self._check(self.lib.nb_get_batched_form(self.h, int(offsets.shape[0]) - 1, _ptr(offsets),
+                                                 ctypes.byref(form)), "nb_get_batched_form")
         return {"threads": out[0], "bodies_per_thread": out[1], "jtile": out[2], "items_per_step": out[3],
-                "ctas": out[4], "tuned": out[5] == 1, "pinned": out[5] == 2}
+                "ctas": out[4], "tuned": out[5] == 1, "pinned": out[5] == 2,
+                "form": {1: "one_sided", 2: "pair_symmetric"}[form.value]}
+
+    def set_batched_form(self, offsets, form: str | None):
+        """Pin the batched form for these sizes ("one_sided", "pair_symmetric"); None clears."""
+        f = {None: 0, "one_sided": 1, "pair_symmetric": 2}[form]
+        self._check(self.lib.nb_set_batched_form(self.h, int(offsets.shape[0]) - 1, _ptr(offsets), f),
+                    "nb_set_batched_form")
 
     def get_run_path(self, n: int) -> dict:
         """The nb_run path for n bodies: graph, cluster or grid, its size, and whether it was tuned."""

@@ -1,6 +1,6 @@
 """Run the batched ensemble once, for timing and profiling.
 
-    python -m paper_2203_08263_gb300.profile_batched [--steps 100] [--tune]
+    python -m paper_2203_08263_gb300.profile_batched [--steps 100] [--tune] [--form pair_symmetric]
 
 Input: 512 uniform-cube systems with N log-uniform in [64, 8192] (seed 3),
 eps = 0.01, dt = 1e-3. Prints the CUDA-event time of one nb_run_batched call
@@ -19,6 +19,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--nsys", type=int, default=512)
     ap.add_argument("--tune", action="store_true", help="autotune the batched shape first")
+    ap.add_argument("--form", default=None, choices=["one_sided", "pair_symmetric"],
+                    help="pin the batched form (default: chosen for the sizes)")
     a = ap.parse_args()
 
     import torch
@@ -33,6 +35,8 @@ def main():
     offt = torch.tensor(off, dtype=torch.int64)
     if a.tune:
         ctx.autotune_batched(offt)
+    if a.form:
+        ctx.set_batched_form(offt, a.form)
     xt, vt, mt = (torch.tensor(t, dtype=torch.float32, device=dev) for t in (x, v, m))
     ctx.run_batched(offt, xt.clone(), vt.clone(), mt, 1)  # plan and capture
     torch.cuda.synchronize()

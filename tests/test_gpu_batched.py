@@ -67,7 +67,10 @@ def test_autotuned_batched_shape(nbm):
     ctx.autotune_batched(offt)
     cfg = ctx.get_batched_config(offt)
     assert cfg["tuned"] and cfg["threads"] in (128, 256, 512)
-    assert cfg["bodies_per_thread"] in (1, 2, 4, 8) and cfg["jtile"] in (64, 128)
+    if cfg["form"] == "one_sided":
+        assert cfg["bodies_per_thread"] in (1, 2, 4, 8) and cfg["jtile"] in (64, 128)
+    else:
+        assert (cfg["threads"], cfg["bodies_per_thread"], cfg["jtile"]) == (128, 8, 256)
     xt = torch.tensor(x, dtype=torch.float32, device=DEV)
     vt = torch.tensor(v, dtype=torch.float32, device=DEV)
     mt = torch.tensor(m, dtype=torch.float32, device=DEV)
@@ -173,7 +176,8 @@ def test_batched_precision_form_every_system(nbm, scheme):
     vt = torch.tensor(v, dtype=torch.float64, device=DEV)
     mt = torch.tensor(m, dtype=torch.float64, device=DEV)
     offt = torch.tensor(off, dtype=torch.int64)
-    assert ctx.get_batched_config(offt)["bodies_per_thread"] <= 4
+    cfg = ctx.get_batched_config(offt)
+    assert cfg["form"] == "pair_symmetric" or cfg["bodies_per_thread"] <= 4
     ctx.run_batched(offt, xt, vt, mt, 10)
     ctx.sync()
     gx, gv = to_np(xt), to_np(vt)
@@ -192,7 +196,7 @@ def test_batched_precision_form_tuned_and_pinned(nbm):
         ctx.set_batched_config(offt, 256, 8, 64)  # above 4 bodies per thread
     ctx.autotune_batched(offt)
     cfg = ctx.get_batched_config(offt)
-    assert cfg["tuned"] and cfg["bodies_per_thread"] <= 4
+    assert cfg["tuned"] and (cfg["form"] == "pair_symmetric" or cfg["bodies_per_thread"] <= 4)
     xt = torch.tensor(x, dtype=torch.float64, device=DEV)
     vt = torch.tensor(v, dtype=torch.float64, device=DEV)
     mt = torch.tensor(m, dtype=torch.float64, device=DEV)
@@ -202,3 +206,106 @@ def test_batched_precision_form_tuned_and_pinned(nbm):
         a, b = off[s_], off[s_ + 1]
         xr, _ = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 4)
         assert rel_l2(to_np(xt)[a:b], xr) <= 1e-9
+
+
+# ------------------------------------------------- pair-symmetric form
+
+SYM_SIZES = [1, 0, 2, 3, 65, 130, 0, 255, 256, 257, 33, 300, 513, 1000, 2047]
+
+
+def _ens(sizes, seed, plummer=False):
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    if plummer:
+        parts = [ics.plummer(n, seed=seed + k) for k, n in enumerate(sizes) if n > 0]
+        x = np.concatenate([p.x for p in parts])
+        v = np.concatenate([p.v for p in parts])
+        m = np.concatenate([p.m for p in parts])
+        return off, x, v, m
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, (off[-1], 3))
+    v = rng.uniform(-0.1, 0.1, (off[-1], 3))
+    m = rng.uniform(0.5, 1.5, off[-1]) / 1000
+    return off, x, v, m
+
+
+@pytest.mark.parametrize("scheme", ["paper", "kdk"])
+def test_sym_ensemble_every_system(nbm, scheme):
+    """The pair-symmetric ensemble form (groups of 256 bodies, one item per
+    pair of groups and one epilogue item per group): every system of a batch
+    with empty, tiny, exact-group and multi-group systems against its own
+    oracle run."""
+    off, x, v, m = _ens(SYM_SIZES, 7)
+    ctx = nbm.Context(0.9, 0.02, 2e-3, scheme=scheme)
+    offt = torch.tensor(off, dtype=torch.int64)
+    ctx.set_batched_form(offt, "pair_symmetric")
+    cfg = ctx.get_batched_config(offt)
+    assert cfg["form"] == "pair_symmetric" and cfg["pinned"]
+    xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float32, device=DEV)
+    ctx.run_batched(offt, xt, vt, mt, 6)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s in range(len(SYM_SIZES)):
+        a, b = off[s], off[s + 1]
+        if b == a:
+            continue
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 0.9, 0.02, 2e-3, 6, scheme=scheme)
+        assert rel_l2(gx[a:b], xr) <= 1e-5, (s, SYM_SIZES[s])
+        assert rel_l2(gv[a:b], vr) <= 1e-4, (s, SYM_SIZES[s])
+
+
+def test_sym_ensemble_precision_form(nbm):
+    sizes = [3, 200, 1000, 1500, 2100, 700]
+    off, x, v, m = _ens(sizes, 60, plummer=True)
+    ctx = nbm.Context(1.0, 0.05, 5e-4, precision="comp")
+    offt = torch.tensor(off, dtype=torch.int64)
+    ctx.set_batched_form(offt, "pair_symmetric")
+    xt = torch.tensor(x, dtype=torch.float64, device=DEV)
+    vt = torch.tensor(v, dtype=torch.float64, device=DEV)
+    mt = torch.tensor(m, dtype=torch.float64, device=DEV)
+    ctx.run_batched(offt, xt, vt, mt, 10)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s_ in range(len(sizes)):
+        a, b = off[s_], off[s_ + 1]
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.05, 5e-4, 10)
+        assert rel_l2(gx[a:b], xr) <= 1e-9, s_
+        assert rel_l2(gv[a:b], vr) <= 1e-6, s_
+
+
+def test_sym_ensemble_deterministic_and_agrees_with_one_sided(nbm):
+    off, x, v, m = ics.ensemble(nsys=30, seed=5, nmin=64, nmax=3000)
+    offt = torch.tensor(off, dtype=torch.int64)
+    res = {}
+    for form in ("pair_symmetric", "pair_symmetric", "one_sided"):
+        ctx = nbm.Context(1.0, 0.01, 1e-3)
+        ctx.set_batched_form(offt, form)
+        xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+        vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+        mt = torch.tensor(m, dtype=torch.float32, device=DEV)
+        ctx.run_batched(offt, xt, vt, mt, 5)
+        ctx.sync()
+        res.setdefault(form, []).append((to_np(xt), to_np(vt)))
+    (x1, v1), (x2, v2) = res["pair_symmetric"]
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)  # bit-identical repeats
+    xo, vo = res["one_sided"][0]
+    assert rel_l2(x1, xo) <= 1e-6 and rel_l2(v1, vo) <= 1e-5
+
+
+def test_batched_form_default_and_pins(nbm):
+    """Default form by the work estimate: pair-symmetric for the C4 size mix,
+    one-sided for systems of 64 bodies; pins and their removal."""
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    off, _, _, _ = ics.ensemble(nsys=512, seed=3)
+    offt = torch.tensor(off, dtype=torch.int64)
+    assert ctx.get_batched_config(offt)["form"] == "pair_symmetric"
+    small = torch.tensor(np.arange(0, 64 * 41, 64), dtype=torch.int64)
+    assert ctx.get_batched_config(small)["form"] == "one_sided"
+    ctx.set_batched_form(small, "pair_symmetric")
+    assert ctx.get_batched_config(small)["form"] == "pair_symmetric"
+    ctx.set_batched_config(small, 256, 4, 64)  # a one-sided shape pins the one-sided form
+    cfg = ctx.get_batched_config(small)
+    assert cfg["form"] == "one_sided" and cfg["pinned"] and cfg["threads"] == 256
+    ctx.set_batched_form(small, None)
+    assert not ctx.get_batched_config(small)["pinned"]
