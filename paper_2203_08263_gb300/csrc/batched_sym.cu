@@ -36,7 +36,10 @@ namespace {
 constexpr int kGrp = 256;  // bodies per group: 32 lanes x kGR
 constexpr int kGR = 8;
 constexpr int kSymWarps = 4;  // warps per CTA
-constexpr int kHoldW = 4;     // items a warp may hold unstarted
+#ifndef NB_SYMB_HOLD
+#define NB_SYMB_HOLD 2  // measured on the 512-system ensemble: 3.01e12 interactions/s at 2, 2.93e12 at 4, 2.92e12 at 8
+#endif
+constexpr int kHoldW = NB_SYMB_HOLD;  // items a warp may hold unstarted
 constexpr unsigned kNone = 0xFFFFFFFFu;
 #ifndef NB_SYMB_MINB
 #define NB_SYMB_MINB 3  // resident CTAs per SM the FP32 kernel's registers are sized for (4: 128 registers, 2.72e12 interactions/s on the 512-system ensemble against 2.94e12 at 3)
