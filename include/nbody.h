@@ -306,9 +306,11 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * many nanoseconds (default 2e9; 0 gives up at the first poll that returns
  * without the phase complete). NB_DBG_STALL_PRODUCER (value 0/1): the
  * pair-sum kernels issue no j-tile copies, so every tile wait of nb_accel,
- * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out, and in
+ * nb_step, nb_run, nb_vjp, nb_adjoint and nb_energy runs out, in
  * nb_run's grid form CTA 0 never arrives at the step barrier, so every
- * barrier wait runs out; with a short timeout this exercises the error path
+ * barrier wait runs out, and in nb_run_batched's pair-symmetric form one
+ * warp never releases its first work item, so every item waiting for it runs
+ * out its wait; with a short timeout this exercises the error path
  * without hanging (results are then invalid and nb_sync returns
  * NB_ERR_TIMEOUT). */
 typedef enum {

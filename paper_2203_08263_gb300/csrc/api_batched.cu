@@ -69,15 +69,16 @@ nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x,
     NB_CUDA(batched_upload(plan, ctx->bat.p, st));
     char key[512];
     const int kdk = ctx->p.scheme == NB_SCHEME_KDK ? 1 : 0;
-    snprintf(key, sizeof key, "bat|%d|%p|%p|%p|%d|%d|%lld|%llx|%llu|%a|%a|%a", nsys, x, v, m, steps,
+    snprintf(key, sizeof key, "bat|%d|%p|%p|%p|%d|%d|%lld|%llx|%llu|%d|%a|%a|%a", nsys, x, v, m, steps,
              kdk, (long long)total, (unsigned long long)plan.signature,
-             (unsigned long long)ctx->timeout_ns, ctx->p.G, ctx->p.eps, ctx->p.dt);
+             (unsigned long long)ctx->timeout_ns, ctx->debug, ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
         NB_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = batched_enqueue(plan, ctx->bat.p, x, v, m, steps, kdk,
                                          (float)(ctx->p.eps * ctx->p.eps), ctx->p.G, ctx->p.dt,
-                                         ctx->err_word, ctx->timeout_ns, ctx->side);
+                                         ctx->err_word, ctx->timeout_ns,
+                                         (ctx->debug & kDbgStallProducer) ? 1 : 0, ctx->side);
         cudaGraph_t graph = nullptr;
         cudaError_t ce2 = cudaStreamEndCapture(ctx->side, &graph);
         if (ce != cudaSuccess || ce2 != cudaSuccess) {
@@ -138,10 +139,10 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
             NB_CUDA(batched_fill_synthetic(plan, ctx->bat.p, x, v, m, st));
             const float eps2 = (float)(ctx->p.eps * ctx->p.eps);
             NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, 1, 0, eps2, ctx->p.G,
-                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, 0, st));
             NB_CUDA(cudaEventRecord(e0, st));
             NB_CUDA(batched_enqueue(plan, ctx->bat.p, x, v, m, probe_steps, 0, eps2, ctx->p.G,
-                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, st));
+                                    ctx->p.dt, ctx->err_word, ctx->timeout_ns, 0, st));
             NB_CUDA(cudaEventRecord(e1, st));
             NB_CUDA(cudaEventSynchronize(e1));
             ctx->launches += 6;

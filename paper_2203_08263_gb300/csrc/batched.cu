@@ -614,8 +614,9 @@ cudaError_t batched_fill_synthetic(const BatchPlan &p, void *scratch, void *x, v
 
 cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, void *x, void *v, const void *m,
                             int steps, int kdk, float eps2, double G, double dt, int *err,
-                            uint64_t timeout_ns, cudaStream_t st) {
-    if (p.sym) return batched_sym_enqueue(p, scratch, x, v, m, steps, kdk, eps2, G, dt, err, timeout_ns, st);
+                            uint64_t timeout_ns, int stall, cudaStream_t st) {
+    if (p.sym)
+        return batched_sym_enqueue(p, scratch, x, v, m, steps, kdk, eps2, G, dt, err, timeout_ns, stall, st);
     if ((uint64_t)p.items_per_step * (uint64_t)(steps + 1) + (uint64_t)p.ncta * (kHold + 1) >= (1ull << 32))
         return cudaErrorInvalidValue;
     Layout L = layout_of(p);

@@ -51,7 +51,7 @@ cudaError_t batched_sym_upload(const BatchPlan &plan, void *scratch, cudaStream_
 const int64_t *batched_sym_offsets(const BatchPlan &plan, void *scratch);
 cudaError_t batched_sym_enqueue(const BatchPlan &plan, void *scratch, void *x, void *v,
                                 const void *m, int steps, int kdk, float eps2, double G, double dt,
-                                int *err, uint64_t timeout_ns, cudaStream_t st);
+                                int *err, uint64_t timeout_ns, int stall, cudaStream_t st);
 
 // Build the plan for the given offsets on this device. Shape fields of
 // `plan` (nt, r, jt) may be preset; plan.sym = 1 builds the pair-symmetric
@@ -68,9 +68,11 @@ cudaError_t batched_fill_synthetic(const BatchPlan &plan, void *scratch, void *x
                                    cudaStream_t st);
 // Zero the queue and completion counters, pack every system, launch the
 // persistent kernel for `steps` steps of the paper scheme (kdk = 0) or of
-// kick-drift-kick (kdk = 1).
+// kick-drift-kick (kdk = 1). stall (debug, the pair-symmetric form): one warp
+// never releases its first item, so the items waiting for it run out their
+// wait limit.
 cudaError_t batched_enqueue(const BatchPlan &plan, void *scratch, void *x, void *v,
                             const void *m, int steps, int kdk, float eps2, double G, double dt,
-                            int *err, uint64_t timeout_ns, cudaStream_t st);
+                            int *err, uint64_t timeout_ns, int stall, cudaStream_t st);
 
 }  // namespace nb

@@ -63,6 +63,7 @@ struct SymBatchArgs {
     double Gd, dtd;
     int *err;
     uint64_t timeout_ns;
+    int stall;  // debug: warp 0 of CTA 0 never releases its first item
 };
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(kSymWarps * 32, F64 ? 3 : NB_SYMB_MINB) batche
         }
     };
 
+    bool hold_back = a.stall && blockIdx.x == 0 && threadIdx.x < 32;  // debug: skip the first release
     for (;;) {
         unsigned id = 0, pending = kNone;  // lane 0: a number taken during the item, filed after it
         int ab = 0;
@@ -376,9 +378,10 @@ __global__ void __launch_bounds__(kSymWarps * 32, F64 ? 3 : NB_SYMB_MINB) batche
         __threadfence();
         __syncwarp();
         if (lane == 0) {
-            atomicAdd(it.w == 0 ? a.pair_done + s : a.fin_done + s, 1u);
+            if (!hold_back) atomicAdd(it.w == 0 ? a.pair_done + s : a.fin_done + s, 1u);
             if (pending != kNone) file(pending);
         }
+        hold_back = false;
     }
 }
 
@@ -537,7 +540,7 @@ const int64_t *batched_sym_offsets(const BatchPlan &p, void *scratch) {
 
 cudaError_t batched_sym_enqueue(const BatchPlan &p, void *scratch, void *x, void *v, const void *m,
                                 int steps, int kdk, float eps2, double G, double dt, int *err,
-                                uint64_t timeout_ns, cudaStream_t st) {
+                                uint64_t timeout_ns, int stall, cudaStream_t st) {
     if ((uint64_t)p.items_per_step * (uint64_t)(steps + 1) + (uint64_t)p.ncta * kSymWarps * (kHoldW + 1) >=
         (1ull << 32))
         return cudaErrorInvalidValue;
@@ -568,6 +571,7 @@ cudaError_t batched_sym_enqueue(const BatchPlan &p, void *scratch, void *x, void
     a.dtd = dt;
     a.err = err;
     a.timeout_ns = timeout_ns;
+    a.stall = stall;
     cudaError_t e = cudaMemsetAsync(b + L.o_next, 0, L.o_xm0 - L.o_next, st);
     if (e != cudaSuccess) return e;
     if (p.f64)

@@ -309,3 +309,35 @@ def test_batched_form_default_and_pins(nbm):
     assert cfg["form"] == "one_sided" and cfg["pinned"] and cfg["threads"] == 256
     ctx.set_batched_form(small, None)
     assert not ctx.get_batched_config(small)["pinned"]
+
+
+def test_sym_ensemble_wait_timeout_is_reported(nbm):
+    """Pair-symmetric form with one warp holding back the release of its first
+    item (a debug flag): the items that depend on it give up after 1 ms each,
+    nb_sync reports NB_ERR_TIMEOUT, and the context then runs correctly."""
+    sizes = [700, 300, 1000]
+    off, x, v, m = _ens(sizes, 3)
+    ctx = nbm.Context(1.0, 0.01, 1e-3)
+    offt = torch.tensor(off, dtype=torch.int64)
+    ctx.set_batched_form(offt, "pair_symmetric")
+
+    def state():
+        return (torch.tensor(x, dtype=torch.float32, device=DEV), torch.tensor(v, dtype=torch.float32, device=DEV),
+                torch.tensor(m, dtype=torch.float32, device=DEV))
+
+    ctx.debug_set(nbm.NB_DBG_WAIT_TIMEOUT_NS, 1_000_000)
+    ctx.debug_set(nbm.NB_DBG_STALL_PRODUCER, 1)
+    xt, vt, mt = state()
+    ctx.run_batched(offt, xt, vt, mt, 3)
+    with pytest.raises(nbm.NBodyError) as ei:
+        ctx.sync()
+    assert ei.value.status == nbm.NB_ERR_TIMEOUT
+    ctx.debug_set(nbm.NB_DBG_STALL_PRODUCER, 0)
+    ctx.debug_set(nbm.NB_DBG_WAIT_TIMEOUT_NS, 2_000_000_000)
+    xt, vt, mt = state()
+    ctx.run_batched(offt, xt, vt, mt, 3)
+    ctx.sync()
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        xr, _ = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 3)
+        assert rel_l2(to_np(xt)[a:b], xr) <= 1e-5, s
