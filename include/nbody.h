@@ -170,9 +170,10 @@ nb_status nb_run(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, int st
  * partials in group order and runs the update; a warp runs one item. In
  * FP32 the pair-symmetric form is the default when its work, padding
  * included, is below 0.85 of the one-sided form's (ensembles of systems of a
- * few hundred bodies and more), and nb_autotune_batched times both; the
- * precision form runs it only when pinned (its FP32 partials are longer
- * sums than the one-sided tiles').
+ * few hundred bodies and more) and its group-pair partials (sum over systems
+ * of 12 x 256 x groups^2 bytes) fit in 16 GiB, and nb_autotune_batched times
+ * both; the precision form runs it only when pinned (its FP32 partials are
+ * longer sums than the one-sided tiles').
  */
 nb_status nb_run_batched(nb_ctx *ctx, int nsys, const int64_t *offsets, void *x, void *v,
                          const void *m, int steps, void *stream);

@@ -22,7 +22,8 @@ namespace {
 // keeps the one-sided items unless pinned: the pair-symmetric items sum up to
 // 256 terms per FP32 partial against the one-sided tiles' 32 to 128, which
 // shows on close encounters (cube, eps = 0.01: positions after 4 steps
-// 4.4e-9 from the FP64 oracle against below 1e-9).
+// 4.4e-9 from the FP64 oracle against below 1e-9). Sizes whose partials
+// would exceed the single-system form's cap keep the one-sided items.
 void preset_plan(nb_ctx *ctx, const std::vector<int64_t> &off, BatchPlan &plan) {
     plan.f64 = f64_state(ctx) ? 1 : 0;
     auto tuned = ctx->batched_tuned.find(sizes_signature(off));
@@ -34,7 +35,9 @@ void preset_plan(nb_ctx *ctx, const std::vector<int64_t> &off, BatchPlan &plan) 
         plan.sym = tuned->second.sym;
         return;
     }
-    plan.sym = !plan.f64 && batched_sym_work_ratio(off) < 0.85 ? 1 : 0;
+    plan.sym = !plan.f64 && batched_sym_work_ratio(off) < 0.85 && batched_sym_part_bytes(off) <= kSymMaxPartBytes
+                   ? 1
+                   : 0;
 }
 
 }  // namespace

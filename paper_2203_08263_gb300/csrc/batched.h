@@ -46,6 +46,9 @@ int64_t batched_max_n();
 // FP32 lane operations of the pair-symmetric form over those of the one-sided
 // form for these system sizes (the padding to whole groups included).
 double batched_sym_work_ratio(const std::vector<int64_t> &off);
+// Bytes of group-pair partials the pair-symmetric form keeps for these sizes
+// (sum over systems of groups^2 x 3 x 256 floats).
+size_t batched_sym_part_bytes(const std::vector<int64_t> &off);
 bool batched_sym_plan(int num_sms, const std::vector<int64_t> &off, BatchPlan &plan, std::string &why);
 cudaError_t batched_sym_upload(const BatchPlan &plan, void *scratch, cudaStream_t st);
 const int64_t *batched_sym_offsets(const BatchPlan &plan, void *scratch);

@@ -27,7 +27,7 @@
 #include <cstring>
 
 #include "batched.h"
-#include "engine.cuh"
+#include "kernels.h"
 
 namespace nb {
 
@@ -435,6 +435,15 @@ SymLayout sym_layout_of(const BatchPlan &p) {
 
 }  // namespace
 
+size_t batched_sym_part_bytes(const std::vector<int64_t> &off) {
+    size_t floats = 0;
+    for (size_t s = 0; s + 1 < off.size(); ++s) {
+        const size_t g = (size_t)((off[s + 1] - off[s] + kGrp - 1) / kGrp);
+        floats += g * 3 * g * kGrp;
+    }
+    return floats * 4;
+}
+
 double batched_sym_work_ratio(const std::vector<int64_t> &off) {
     // FP32 lane operations of the pair-symmetric items (16 per evaluated pair,
     // groups padded to kGrp) against the one-sided items' (12 per interaction)
@@ -450,6 +459,10 @@ double batched_sym_work_ratio(const std::vector<int64_t> &off) {
 
 bool batched_sym_plan(int num_sms, const std::vector<int64_t> &off, BatchPlan &p, std::string &why) {
     p.sym = 1;
+    if (batched_sym_part_bytes(off) > kSymMaxPartBytes) {
+        why = "the pair-symmetric form's partials for these sizes exceed 16 GiB";
+        return false;
+    }
     p.nsys = (int)off.size() - 1;
     p.nt = kSymWarps * 32;
     p.r = kGR;

@@ -309,6 +309,11 @@ def test_batched_form_default_and_pins(nbm):
     assert cfg["form"] == "one_sided" and cfg["pinned"] and cfg["threads"] == 256
     ctx.set_batched_form(small, None)
     assert not ctx.get_batched_config(small)["pinned"]
+    # one system of 2^20 bodies: its group-pair partials (48 GiB) exceed the cap
+    big = torch.tensor([0, 1 << 20], dtype=torch.int64)
+    assert ctx.get_batched_config(big)["form"] == "one_sided"
+    with pytest.raises(nbm.NBodyError):
+        ctx.set_batched_form(big, "pair_symmetric")
 
 
 def test_sym_ensemble_wait_timeout_is_reported(nbm):
