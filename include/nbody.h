@@ -256,9 +256,11 @@ nb_status nb_energy(nb_ctx *ctx, int64_t n, const void *x, const void *v, const 
 /*
  * Time the candidate kernel shapes for problems of size n in mode `mode`
  * (0 = forward, 1 = adjoint VJP) and store the fastest in the context's
- * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set). In
- * mode 0 with n <= 8192 it also times nb_run's paths
- * (graph of force launches, one-cluster kernel) and records the faster. Calls
+ * table (and in the JSON file named by $NB_AUTOTUNE_CACHE when set): every
+ * compiled one-sided shape with its j-tile and split, and from n = 8192
+ * (forward; 2048 for the FP32 VJP) the pair-symmetric kernels at each block
+ * size. In mode 0 with n <= 8192 it also times nb_run's paths (graph of force
+ * launches, one-cluster kernel, grid form) and records the fastest. Calls
  * that find no entry for their size bucket use a built-in heuristic instead.
  * Synchronous.
  */
