@@ -1,5 +1,6 @@
-// All-pairs tile engine: one kernel template serves every pair sum of the
-// library (forces, compensated forces, potential, adjoint VJP).
+// All-pairs tile engine: one kernel template serves every one-sided pair sum
+// of the library (forces, compensated forces, potential, adjoint VJP); the
+// pair-symmetric kernels (csrc/k_sym.cu) reuse its helpers and epilogues.
 //
 // Work decomposition. Bodies are packed in a "pair layout" (two bodies per
 // 32-byte record for the force sums: {x0,x1,y0,y1}, {z0,z1,m0,m1}) and padded
