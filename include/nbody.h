@@ -112,7 +112,7 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  *
  * Force forms (the same sum in every form; nb_get_form tells which one
  * serves a size). A one-sided kernel sums over j for every i. From
- * n = 32768 up (or where nb_autotune finds it faster) a pair-symmetric
+ * n = 16384 up (or where nb_autotune finds it faster) a pair-symmetric
  * kernel evaluates each unordered pair {i, j} once and adds its term to both
  * bodies with opposite signs (Newton's third law), into per-block partials
  * that a second kernel adds in a fixed order: in FP32, and in the precision

@@ -37,7 +37,7 @@ constexpr int kGrp = 256;  // bodies per group: 32 lanes x kGR
 constexpr int kGR = 8;
 constexpr int kSymWarps = 4;  // warps per CTA
 #ifndef NB_SYMB_HOLD
-#define NB_SYMB_HOLD 2  // measured on the 512-system ensemble: 3.01e12 interactions/s at 2, 2.93e12 at 4, 2.92e12 at 8
+#define NB_SYMB_HOLD 1  // measured on the 512-system ensemble: 3.15e12-3.17e12 interactions/s at 1, 2.99e12-3.01e12 at 2, 2.93e12 at 4, 2.92e12 at 8
 #endif
 constexpr int kHoldW = NB_SYMB_HOLD;  // items a warp may hold unstarted
 constexpr unsigned kNone = 0xFFFFFFFFu;

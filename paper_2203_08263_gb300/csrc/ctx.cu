@@ -192,7 +192,7 @@ Shape finish_shape(const nb_ctx *ctx, int pol, int nt, int r, int jt, int split_
 Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     const int pol = mode_pol(ctx, mode);
     int nt = 128, r = 1, jt = 64;
-    if ((pol == kPolF32x2 || pol == kPolComp) && allow_sym && n >= 32768) {
+    if ((pol == kPolF32x2 || pol == kPolComp) && allow_sym && n >= 16384) {
         // each unordered pair once, blocks of 1024 bodies from 2^17 up (enough
         // block pairs to fill the GPU), 512 below; the one-sided policy above
         // the partial-buffer cap

@@ -22,9 +22,11 @@ def main():
     ap.add_argument("--n", type=int, default=65536)
     ap.add_argument("--shape", default="0,0,0,0", help="threads,bodies_per_thread,split,jtile (0 = auto)")
     ap.add_argument("--pol", default="fp32",
-                    choices=["fp32", "comp", "vjp", "vjp-comp", "energy", "step", "step-comp"])
+                    choices=["fp32", "comp", "vjp", "vjp-comp", "energy", "step", "step-comp", "adjoint"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--steps", type=int, default=1, help="paper steps per call for --pol step / step-comp")
+    ap.add_argument("--steps", type=int, default=1,
+                    help="paper steps per call for --pol step / step-comp; T for --pol adjoint")
+    ap.add_argument("--ckpt-every", type=int, default=20, help="checkpoint interval for --pol adjoint")
     ap.add_argument("--path", type=int, default=0,
                     help="nb_run path for --pol step / step-comp: 0 chosen per size, 1 graph, 2 one cluster")
     ap.add_argument("--form", type=int, default=0,
@@ -58,7 +60,14 @@ def main():
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,
-            "energy": MODE_POTENTIAL, "step": MODE_FORWARD, "step-comp": MODE_FORWARD}[a.pol]
+            "energy": MODE_POTENTIAL, "step": MODE_FORWARD, "step-comp": MODE_FORWARD,
+            "adjoint": MODE_ADJOINT}[a.pol]
+    if a.pol == "adjoint":  # a trajectory with checkpoints, then its reverse sweep (timed)
+        k = a.ckpt_every
+        ck = torch.empty((a.steps // k + 1, a.n, 6), dtype=f, device=dev)
+        ctx.run(x, v, m, a.steps, ckpt=ck, ckpt_every=k)
+        xb = torch.tensor(np.random.default_rng(1).normal(size=(a.n, 3)), dtype=f, device=dev)
+        vb = torch.zeros_like(xb)
 
     def call():
         if a.pol in ("fp32", "comp"):
@@ -67,6 +76,8 @@ def main():
             ctx.vjp(x, m, ab)
         elif a.pol in ("step", "step-comp"):
             ctx.run(x, v, m, a.steps)  # paper steps: pack + force sums with the kick/drift epilogue
+        elif a.pol == "adjoint":
+            ctx.adjoint(m, a.steps, ck, a.ckpt_every, xb, vb)
         else:
             ctx.energy(x, v, m)
 
@@ -82,7 +93,7 @@ def main():
         times.append(e0.elapsed_time(e1) / 1e3)
     ctx.sync()
     t = min(times)
-    inter = float(a.n) ** 2 * (a.steps if a.pol in ("step", "step-comp") else 1)
+    inter = float(a.n) ** 2 * (a.steps if a.pol in ("step", "step-comp", "adjoint") else 1)
     print(json.dumps({"n": a.n, "pol": a.pol, "shape": ctx.get_config(a.n, mode), "s": t, "times": times,
                       "interactions_per_s": inter / t, "tflops_20": 20 * inter / t / 1e12}))
 

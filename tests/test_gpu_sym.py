@@ -111,20 +111,20 @@ def test_sym_is_deterministic(nbm):
 
 
 def test_default_form_by_size(nbm):
-    """Untuned forward, both precisions: one-sided below 32768 bodies,
+    """Untuned forward, both precisions: one-sided below 16384 bodies,
     pair-symmetric from there, one-sided when pinned; the VJP from 8192."""
     ctx = nbm.Context(1.0, 0.01, 1e-3)
     if ctx.get_config(40000)["tuned"]:
         pytest.skip("a tuning table is loaded")
-    assert ctx.get_config(20000)["form"] == "f32x2"
-    assert ctx.get_config(40000)["form"] == "pair_symmetric"
+    assert ctx.get_config(12000)["form"] == "f32x2"
+    assert ctx.get_config(20000)["form"] == "pair_symmetric"
     assert ctx.get_config(4000, nbm.MODE_ADJOINT)["form"] == "vjp"
     assert ctx.get_config(9000, nbm.MODE_ADJOINT)["form"] == "vjp_pair_symmetric"
     ctx.debug_set(nbm.NB_DBG_FORM, 1)
     assert ctx.get_config(40000)["form"] == "f32x2"
     comp = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
-    assert comp.get_config(20000)["form"] == "compensated"
-    assert comp.get_config(40000)["form"] == "compensated_pair_symmetric"
+    assert comp.get_config(12000)["form"] == "compensated"
+    assert comp.get_config(20000)["form"] == "compensated_pair_symmetric"
     comp.debug_set(nbm.NB_DBG_FORM, 1)
     assert comp.get_config(40000)["form"] == "compensated"
     assert comp.get_config(40000, nbm.MODE_ADJOINT)["form"] == "vjp_compensated"
