@@ -54,6 +54,7 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 // Forces.
 struct SymAccel {
     static constexpr int R = kSymR;
+    static constexpr int REGS = 128;  // register target: 4 CTAs of 4 warps per SM (126 used)
     static constexpr int NACC = 3;      // a_x, a_y, a_z
     static constexpr int REC_F4 = 2;    // {x0,x1,y0,y1} {z0,z1,m0,m1}
     static constexpr bool SELF_MASK = false;  // d = 0 gives exactly 0
@@ -131,8 +132,12 @@ struct SymComp : SymAccel {
 
 // Adjoint VJP: sums (U_x, U_y, U_z, V, W_x, W_y, W_z, P), records as the
 // one-sided VJP's {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1} {az0,az1,0,0}.
+#ifndef NB_SYM_VJP_REGS
+#define NB_SYM_VJP_REGS 168  // 3 CTAs of 4 warps per SM; 128 (4 CTAs) spills: 52.3 against 49.2 ms for the N = 16384 adjoint
+#endif
 struct SymVjp {
     static constexpr int R = kSymVjpR;
+    static constexpr int REGS = NB_SYM_VJP_REGS;  // register target
     static constexpr int NACC = 8;
     static constexpr int REC_F4 = 4;
     static constexpr bool SELF_MASK = true;
@@ -263,8 +268,16 @@ __device__ __forceinline__ void chunk_rounds(typename S::J &sj, const typename S
     }
 }
 
+// Resident CTAs per SM that keep a policy's registers at its target (the
+// compiler's own choice without a bound; a bound of 1 CTA let it take 210 for
+// the VJP).
 template <class S, int W>
-__global__ void __launch_bounds__(W * 32) sym_kernel(const ForceArgs a) {
+constexpr int sym_min_blocks() {
+    return 65536 / (W * 32 * S::REGS) > 0 ? 65536 / (W * 32 * S::REGS) : 1;
+}
+
+template <class S, int W>
+__global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(const ForceArgs a) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
     extern __shared__ float acc_j[];  // [W][NA][B]
     // the previous kernel on the stream (last step's epilogue reads P and
