@@ -239,9 +239,10 @@ __device__ __forceinline__ void sym_item(int t, int nb, int &bi, int &bj) {
 }
 
 // The 32 rounds of one chunk. MASK: the diagonal item of a policy that
-// masks its own pair; i_off[r] and j_off are offsets within the block.
+// masks its own pair; i_base (this lane's first i-body) and j_base (the
+// chunk's first j-body) are offsets within the block.
 #ifndef NB_SYM_ROUND_UNROLL
-#define NB_SYM_ROUND_UNROLL 1
+#define NB_SYM_ROUND_UNROLL 1  // two rounds per unrolled step measured within noise
 #endif
 constexpr int kRoundUnroll = NB_SYM_ROUND_UNROLL;  // rounds per unrolled step (build flag)
 
