@@ -118,7 +118,7 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  * that a second kernel adds in a fixed order: in FP32, and in the precision
  * form with FP32 pair terms and the partials two-summed before the FP64
  * update. It keeps nb x 3 x npad floats of partials in the context
- * (nb = npad / B blocks of B = 512 or 1024 bodies, npad = n rounded up to a
+ * (nb = npad / B blocks of B = 256, 512 or 1024 bodies, npad = n rounded up to a
  * block: about 12 n^2 / 1024 bytes, 0.8 GB at n = 262144, 12 GiB at
  * n = 2^20). The FP32 VJP of nb_vjp and nb_adjoint has the same two forms
  * (the pair-symmetric one from n = 8192, blocks of 256 or 512 bodies,
@@ -329,7 +329,7 @@ typedef enum {
      * (NB_ERR_UNSUPPORTED at nb_run when the system does not qualify). */
     NB_DBG_RUN_PATH = 4,
     /* Forward force form (FP32 and the precision form): 0 = chosen per size
-     * (default), 1 = one-sided kernels only, 512 or 1024 = the
+     * (default), 1 = one-sided kernels only, 256, 512 or 1024 = the
      * pair-symmetric kernel with blocks of that many bodies at every size
      * (nb_run's graph path; the fused small-system paths keep their own
      * kernel). */

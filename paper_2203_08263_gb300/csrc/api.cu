@@ -251,7 +251,7 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
     if (key == NB_DBG_FORM) {
         if (value != 0 && value != 1 &&
             !(value % kSymR == 0 && find_entry(kPolSym, (int)(value / kSymR), kSymR)))
-            return fail(ctx, NB_ERR_INVALID, "force form must be 0, 1 or a compiled pair-symmetric block (512, 1024)");
+            return fail(ctx, NB_ERR_INVALID, "force form must be 0, 1 or a compiled pair-symmetric block (256, 512, 1024)");
         ctx->form_pin = (int)value;
         clear_graphs(ctx);
         return NB_OK;

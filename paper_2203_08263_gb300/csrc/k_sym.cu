@@ -448,10 +448,12 @@ int occ_sym(int) {
 
 // Shape (nt, r) = (threads per CTA, bodies per lane); the block is nt x r.
 const ForceEntry kAccel[] = {
+    {32, SymAccel::R, &launch_sym<SymAccel, 1>, &occ_sym<SymAccel, 1>},   // blocks of 256
     {64, SymAccel::R, &launch_sym<SymAccel, 2>, &occ_sym<SymAccel, 2>},   // blocks of 512
     {128, SymAccel::R, &launch_sym<SymAccel, 4>, &occ_sym<SymAccel, 4>},  // blocks of 1024
 };
 const ForceEntry kComp[] = {
+    {32, SymComp::R, &launch_sym<SymComp, 1>, &occ_sym<SymComp, 1>},   // blocks of 256
     {64, SymComp::R, &launch_sym<SymComp, 2>, &occ_sym<SymComp, 2>},   // blocks of 512
     {128, SymComp::R, &launch_sym<SymComp, 4>, &occ_sym<SymComp, 4>},  // blocks of 1024
 };

@@ -25,9 +25,9 @@ enum Pol : int {
 };
 
 // Bodies per lane of the pair-symmetric force policy; its table holds blocks
-// of 32 x R x (2 or 4 warps) = 512 or 1024 bodies (Shape: nt = 64 or 128,
-// r = R, jt = the block, split = 1). The VJP's holds R = 4, blocks of 256 or
-// 512 bodies.
+// of 32 x R x (1, 2 or 4 warps) = 256, 512 or 1024 bodies (Shape: nt = 32,
+// 64 or 128, r = R, jt = the block, split = 1). The VJP's holds R = 4,
+// blocks of 256 or 512 bodies.
 #ifndef NB_SYM_R
 #define NB_SYM_R 8  // measured at N = 262144: 3.70e12 interactions/s at R = 6 (96 registers, 5 CTAs per SM), 3.98e12 at 8, 3.99e12 at 10
 #endif

@@ -36,8 +36,8 @@ def _ctx(nbm, block, G=1.0, eps=0.01, dt=1e-3, scheme="paper"):
 
 # one body (the diagonal item alone), odd sizes, one and several blocks with
 # ragged padding, exact multiples of the block
-@pytest.mark.parametrize("block", [512, 1024])
-@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 511, 512, 513, 1000, 1024, 2047, 3001, 5120])
+@pytest.mark.parametrize("block", [256, 512, 1024])
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 255, 257, 511, 512, 513, 1000, 1024, 2047, 3001, 5120])
 def test_sym_accel_matches_oracle(nbm, block, n):
     G, eps = 0.9, 0.02
     s = ics.cube(n, seed=300 + n)
@@ -66,10 +66,10 @@ def test_sym_accel_plummer_momentum(nbm):
 
 
 @pytest.mark.parametrize("scheme", ["paper", "kdk"])
-@pytest.mark.parametrize("n", [777, 4096])
-def test_sym_run_matches_oracle(nbm, scheme, n):
+@pytest.mark.parametrize("n,block", [(777, 512), (4096, 512), (3000, 256)])
+def test_sym_run_matches_oracle(nbm, scheme, n, block):
     s = ics.cube(n, seed=40 + n)
-    ctx = _ctx(nbm, 512, G=1.0, eps=0.01, dt=1e-3, scheme=scheme)
+    ctx = _ctx(nbm, block, G=1.0, eps=0.01, dt=1e-3, scheme=scheme)
     x, v, m = _t(s.x), _t(s.v), _t(s.m)
     before = ctx.launch_count
     ctx.run(x, v, m, 10)
@@ -260,7 +260,7 @@ def test_sym_adjoint_midsize_matches_one_sided(nbm):
 
 # ----------------------------------------------------- precision form
 
-@pytest.mark.parametrize("block", [512, 1024])
+@pytest.mark.parametrize("block", [256, 512, 1024])
 @pytest.mark.parametrize("n", [2, 33, 1000, 4097, 20000])
 def test_sym_compensated_accel_matches_oracle(nbm, block, n):
     """FP64 state, FP32 pair terms each evaluated once for both bodies, the
