@@ -12,7 +12,8 @@ eps = 0.05, dt = 1e-3 (the paper does not state its initial conditions).
 
 Ablation: the GPU analog of the paper's denominator experiment (Sections
 3.2.6 and 3.3.6): MUFU rsqrt cubed, IEEE sqrt then division, and powf, each
-timed on nb_accel and compared with the FP64 oracle on a subset of bodies.
+timed on nb_accel and compared with the library's precision form (compensated
+sums) on a subset of bodies; the parity tests hold the FP64 oracle.
 """
 from __future__ import annotations
 
@@ -67,21 +68,29 @@ def sweep(steps: int, nmax: int):
 def ablation(n: int):
     import torch
 
-    import oracle
     from paper_2203_08263_gb300 import ics
-    from paper_2203_08263_gb300.nbody import NB_DBG_MATH_VARIANT, Context
+    from paper_2203_08263_gb300.nbody import NB_DBG_FORM, NB_DBG_MATH_VARIANT, Context
 
     dev = torch.device("cuda:0")
     s = ics.plummer(n, seed=1)
     idx = ics.subset_indices(n, 512, 9)
-    ref = oracle.accel(s.x, s.m, 1.0, 0.05, idx)
     x, m = (torch.tensor(a, dtype=torch.float32, device=dev) for a in (s.x, s.m))
-    names = {0: "MUFU rsqrt, y^3", 1: "IEEE sqrt then division", 2: "powf(s, -1.5)"}
-    print("\n| denominator | interactions/s | GFLOPS (20/interaction) | rel. L2 vs FP64 oracle |")
+    # reference: the library's precision form on the same FP32-rounded bodies
+    # (compensated sums, about 3e-8 from an FP64 sum on this input class,
+    # against the FP32 variants' 1e-7 .. 1e-6)
+    comp = Context(1.0, 0.05, 1e-3, precision="comp")
+    ref = comp.accel(x.double(), m.double()).cpu().numpy()[idx]
+    comp.close()
+    names = {0: "MUFU rsqrt, y^3", 1: "IEEE sqrt then division", 2: "powf(s, -1.5)",
+             3: "MUFU rsqrt, y^3, pair-symmetric kernel"}
+    print("\n| denominator | interactions/s | GFLOPS (20/interaction) | rel. L2 vs the precision form |")
     print("|---|---|---|---|")
-    for var in (0, 1, 2):
+    for var in (0, 1, 2, 3):
         ctx = Context(1.0, 0.05, 1e-3)
-        ctx.debug_set(NB_DBG_MATH_VARIANT, var)
+        # the three denominators on the one-sided kernels (the variants have
+        # no pair-symmetric form); then the library's default kernel for n
+        ctx.debug_set(NB_DBG_FORM, 0 if var == 3 else 1)
+        ctx.debug_set(NB_DBG_MATH_VARIANT, 0 if var == 3 else var)
         a = ctx.accel(x, m)
         t = min(_timed(torch, lambda: ctx.accel(x, m)) for _ in range(3))
         err = float(np.linalg.norm(a.double().cpu().numpy()[idx] - ref) / np.linalg.norm(ref))
