@@ -16,8 +16,10 @@
 // makes progress.
 //
 // The unit of work is a warp: each warp of the persistent grid takes item
-// numbers from one atomic counter, holds up to kHoldW of them and runs the
-// lowest-numbered ready one. In a pair item the warp holds the 256 bodies of
+// numbers from one atomic counter, holds up to kHoldW of them (one by
+// default) and runs the lowest-numbered ready one; it takes the next number
+// while an item runs, so the atomic's latency is hidden, and keeps its queue
+// state in shared memory, so the pair loop keeps its registers. In a pair item the warp holds the 256 bodies of
 // group gi, 8 per lane, duplicated in f32x2 registers; group gj's 128 pair
 // records go round the warp in four chunks of 32, one record per lane, for 32
 // rounds each, carrying their running j-side sums with them (shuffles); after
