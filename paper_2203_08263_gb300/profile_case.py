@@ -3,11 +3,16 @@
     python -m paper_2203_08263_gb300.profile_case --n 65536 --shape 128,4,16,256 --pol fp32
     python -m paper_2203_08263_gb300.profile_case --n 1024 --pol step --steps 100 --path 2
     python -m paper_2203_08263_gb300.profile_case --n 262144 --pol step --steps 3 --form 1024
+    python -m paper_2203_08263_gb300.profile_case --n 65536 --pol vjp --vjp-form 512
+    python -m paper_2203_08263_gb300.profile_case --n 16384 --pol adjoint --steps 200
     python -m paper_2203_08263_gb300.profile_case --peaks
 
 Input: Plummer sphere (seed 1), eps = 0.05. Prints the CUDA-event time per
-launch and the rate at 20 flops per interaction. --peaks runs the FFMA,
-f32x2-FMA and MUFU micro-benchmarks instead.
+call and the rate at 20 flops per interaction (--pol adjoint: one nb_adjoint
+over a trajectory of --steps steps checkpointed every --ckpt-every, after
+that trajectory is run). --form / --vjp-form pin the force form (one-sided or
+a pair-symmetric block size). --peaks runs the FFMA, f32x2-FMA and MUFU
+micro-benchmarks instead.
 """
 from __future__ import annotations
 
