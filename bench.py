@@ -40,6 +40,17 @@ def workload(n: int) -> str:
             "one bench step = one paper update (force sum + half kick + drift)")
 
 
+L2_NOTE = ("GPU arm: L2 flushed between timed steps (256 MiB write outside the timed events); "
+           "CPU reference arm: each step a fresh i-sample against the whole j-array")
+
+
+def bench_config(n: int, world: int) -> dict:
+    """The workload keys, identical in both arms (launch details go under
+    "launch" in the GPU arm's line)."""
+    return {"workload": workload(n), "n": n, "l2": L2_NOTE,
+            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas, one per GPU"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,7 +172,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload(n), "n": n},
+        "data": "synthetic", "config": bench_config(n, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"each step: the FP64 oracle's force sum for {sample} i-bodies "
                                    f"against all {n} j-bodies (a bounded sample of one step)"},
@@ -334,27 +345,29 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload(n), "n": n, "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "shape": cfg,
-                   "shape_source": shape_source},
+        "config": bench_config(n, world),
+        "launch": {"shape": cfg, "shape_source": shape_source},
         "roofline": roofline,
         "interactions_per_s_per_gpu": inter * args.steps / (tot_ms / 1e3),
         "gflops_20": FLOPS_PER_INTERACTION * value / 1e9,
         "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
 
-    c3_sample = None
+    c3_sample = c5_check = None
     if rank == 0 and world == 1 and not args.no_extras:
         line["extras"] = extras(ctx, torch, dev, np)
         c3_sample = line["extras"].pop("_c3_sample")
+        c5_check = line["extras"].pop("_c5_check")
     if rank == 0 and world == 1 and not args.no_cpu:
         # the CPU-baseline leg: every oracle call of this arm
         line["cpu_baseline"] = cpu_baseline(n, s.x, s.m, G, eps)
         if "extras" in line:
-            rows = oracle_rows(c3_sample)
+            rows = oracle_rows(c3_sample, c5_check)
             line["extras"]["cpu_oracle_rows"] = rows
             line["extras"]["c3_precision_form"]["accel_rel_l2_vs_fp64_oracle_256_subset"] = \
                 rows["c3_accuracy_sample"]["gpu_accel_rel_l2"]
+            line["extras"]["c5_adjoint"]["gradient_rel_l2_vs_fp64_oracle_n64_T20"] = \
+                rows["c5_gradient_check"]["gpu_gradient_rel_l2"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -371,6 +384,31 @@ def _timed(torch, dev, fn, reps=1):
     b.record()
     torch.cuda.synchronize(dev)
     return a.elapsed_time(b) / 1e3
+
+
+def _adjoint_ratio(c, s, xs, f, T, k, torch, dev):
+    """Wall time of T forward steps with a checkpoint every k (nb_run) and of
+    the reverse sweep with its recompute (nb_adjoint) for the loss
+    sum |x_T - x*|^2, on context c in state dtype f."""
+    n = s.n
+    x0, v0, m = (torch.tensor(a_, dtype=f, device=dev) for a_ in (s.x, s.v, s.m))
+    ck = torch.empty((T // k + 1, n, 6), dtype=f, device=dev)
+    x, v = x0.clone(), v0.clone()
+    c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - torch.tensor(xs, dtype=f, device=dev))
+    vbT = torch.zeros_like(xbT)
+    c.adjoint(m, T, ck, k, xbT, vbT)
+
+    def fwd():
+        x.copy_(x0)
+        v.copy_(v0)
+        c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+
+    tf = _timed(torch, dev, fwd)
+    tb = _timed(torch, dev, lambda: c.adjoint(m, T, ck, k, xbT, vbT))
+    return {"n": n, "T": T, "k": k, "forward_s": tf, "backward_s": tb, "ratio": tb / tf,
+            "forward_interactions_per_s": float(n) * n * T / tf,
+            "forward_shape": c.get_config(n, 0), "vjp_shape": c.get_config(n, 1)}
 
 
 def extras(ctx0, torch, dev, np):
@@ -393,7 +431,7 @@ def extras(ctx0, torch, dev, np):
                        "interactions_per_s": 1024.0 * 1024 * 10 / t, "run_path": c.get_run_path(1024),
                        "graph_path_shape": c.get_config(1024)}
     c.close()
-    # C3: precision form, N = 2^20 Plummer (seed 2), FP64 state, 2 steps
+    # C3: precision form, N = 2^20 Plummer (seed 2), FP64 state, 10 steps
     n = 1 << 20
     s = ics.plummer(n, seed=2)
     c = Context(1.0, 0.05, 5e-4, precision="comp", device=dev.index)
@@ -403,8 +441,8 @@ def extras(ctx0, torch, dev, np):
     idx = ics.subset_indices(n, 256, 2 + 1000)
     out["_c3_sample"] = (s.x, s.m, idx, a.cpu().numpy()[idx])
     c.run(x, v, m, 1)
-    t = _timed(torch, dev, lambda: c.run(x, v, m, 2))
-    out["c3_precision_form"] = {"n": n, "steps": 2, "interactions_per_s": 2 * float(n) * n / t, "s": t,
+    t = _timed(torch, dev, lambda: c.run(x, v, m, 10))
+    out["c3_precision_form"] = {"n": n, "steps": 10, "interactions_per_s": 10 * float(n) * n / t, "s": t,
                                 "shape": c.get_config(n)}
     # diagnostics on the C3 state: P, KE, softened potential (O(N^2)), H'
     t0 = time.perf_counter()
@@ -435,32 +473,35 @@ def extras(ctx0, torch, dev, np):
     for mode in (0, 1):  # forward and VJP shapes from the tuner
         if not c.get_config(n, mode)["tuned"]:
             c.autotune(n, mode)
-    x0, v0, m = (torch.tensor(a_, dtype=torch.float32, device=dev) for a_ in (s.x, s.v, s.m))
-    ck = torch.empty((T // k + 1, n, 6), dtype=torch.float32, device=dev)
-    x, v = x0.clone(), v0.clone()
-    c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
-    xbT = 2 * (x - torch.tensor(xs, dtype=torch.float32, device=dev))
-    vbT = torch.zeros_like(xbT)
-    c.adjoint(m, T, ck, k, xbT, vbT)
-
-    def fwd():
-        x.copy_(x0)
-        v.copy_(v0)
-        c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
-
-    tf = _timed(torch, dev, fwd)
-    tb = _timed(torch, dev, lambda: c.adjoint(m, T, ck, k, xbT, vbT))
-    out["c5_adjoint"] = {"n": n, "T": T, "k": k, "forward_s": tf, "backward_s": tb, "ratio": tb / tf,
-                         "forward_interactions_per_s": float(n) * n * T / tf,
-                         "forward_shape": c.get_config(n, 0), "vjp_shape": c.get_config(n, 1)}
+    out["c5_adjoint"] = _adjoint_ratio(c, s, xs, torch.float32, T, k, torch, dev)
     c.close()
+    # the same adjoint in the precision form (FP64 state and gradients,
+    # compensated FP32 forces and VJP)
+    c = Context(1.0, 0.01, 1e-3, precision="comp", device=dev.index)
+    out["c5_adjoint_precision_form"] = _adjoint_ratio(c, s, xs, torch.float64, T, k, torch, dev)
+    c.close()
+    # gradients at the check size (N = 64, T = 20, k = 20) in both forms, for
+    # the CPU-baseline leg to compare with the FP64 oracle's
+    n, T, k = 64, 20, 20
+    s = ics.cube(n, seed=4, masses="equal")
+    xs = ics.targets(n, seed=4)
+    grads = {}
+    for prec, f in (("fp32", torch.float32), ("comp", torch.float64)):
+        c = Context(1.0, 0.01, 1e-3, precision=prec, device=dev.index)
+        x, v, m = (torch.tensor(a_, dtype=f, device=dev) for a_ in (s.x, s.v, s.m))
+        ck = torch.empty((T // k + 1, n, 6), dtype=f, device=dev)
+        c.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+        xbT = 2 * (x - torch.tensor(xs, dtype=f, device=dev))
+        grads[prec] = [g.double().cpu().numpy() for g in c.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))]
+        c.close()
+    out["_c5_check"] = (s, xs, grads)
     out["fp32_peak_fraction"] = {
         k: FLOPS_PER_INTERACTION * out[k]["interactions_per_s"] / 1e12 / FP32_PEAK_TFLOPS
         for k in ("c1_small", "c3_precision_form", "c4_batched")}
     return out
 
 
-def oracle_rows(c3_sample=None):
+def oracle_rows(c3_sample=None, c5_check=None):
     """The FP64 oracle, as it stands, on bounded samples of the other rows
     (host cores of this machine), for comparison with the GPU rates above; with
     the GPU's C3 forces on the accuracy sample, their error against it."""
@@ -502,6 +543,19 @@ def oracle_rows(c3_sample=None):
     dt = time.perf_counter() - t0
     rows["c5_adjoint"] = {"s": dt, "forward_interactions_per_s": float(n) * n * T / dt,
                           "sample": f"full adjoint (forward + reverse, explicit Jacobian blocks), N={n}, T={T}"}
+    if c5_check is not None:
+        s, xs, grads = c5_check
+        t0 = time.perf_counter()
+        xT, _ = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 20)
+        ref = oracle.adjoint(s.x, s.v, s.m, 1.0, 0.01, 1e-3, 20, 2 * (xT - xs), np.zeros((s.n, 3)))
+        dt = time.perf_counter() - t0
+        rows["c5_gradient_check"] = {
+            "gpu_gradient_rel_l2": {
+                prec: {name: float(np.linalg.norm(g - r) / np.linalg.norm(r))
+                       for name, g, r in zip(("xbar0", "vbar0", "mbar"), grads[prec], ref)}
+                for prec in grads},
+            "s": dt, "sample": "N=64 cube (seed 4), T=20, checkpoint every 20: the FP64 oracle's run and "
+                               "adjoint against the GPU gradients of both forms"}
     rows["cores"] = oracle.num_threads()
     return rows
 

@@ -351,24 +351,31 @@ nb_status nb_measure_peaks(nb_ctx *ctx, double *out3);
 
 /*
  * nb_accel_noalloc: the FP32 force sum of nb_accel for callers that cannot
- * allocate device memory when they need it: code running while a stream
- * capture is active (cudaMalloc is refused in global capture mode), processes
- * whose device memory is owned by a pooling allocator, and services whose
- * footprint must be fixed when the library loads. The paper has no
- * counterpart; this is a deployment variant of nb_accel.
+ * allocate device memory when they need it: processes whose device memory is
+ * owned by a pooling allocator (a raw cudaMalloc there fails or fragments the
+ * pool), and services whose footprint must be fixed when the library loads.
+ * The paper has no counterpart; this is a deployment variant of nb_accel.
  *
  * Needs no context and calls no allocator: its working memory (packed
  * bodies, split partials, tickets) is a file-scope device array of about
  * 4.6 MB, reserved on every GPU that loads the library until the process
  * exits. n must be at most NB_NOALLOC_MAX_N (else NB_ERR_INVALID).
- * x [n][3], m [n], a [n][3]: float32 device pointers on the current device;
+ * x [n][3], m [n], a [n][3]: float32 arrays in device (or managed) memory of
+ * the current device, 4-byte aligned; anything else (NULL, host memory,
+ * another device's memory, a misaligned address) returns NB_ERR_INVALID
+ * before anything is launched, as do eps <= 0 and non-finite G or eps.
  * a = G sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2), asynchronous
  * on `stream`. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and the SM count; make that first call
- * before any stream capture. Every call shares the one array, so calls whose
- * kernels overlap on the GPU (different streams, or different host threads)
- * race and must be serialised by the caller. Device-side wait failures are
- * not reported (the error word is cleared by the next call).
+ * address (cudaGetSymbolAddress) and the SM count, once per device (threads
+ * making their first calls at the same time are serialised); make that first
+ * call before any stream capture. A cudaDeviceReset after the first call is
+ * not supported (the looked-up address is kept). Every call shares the one
+ * array and clears its tickets at the start, so calls whose kernels overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller. A device-side wait that gives up (a bulk copy
+ * that has not landed after 2 s) leaves `a` partly written and is not
+ * reported: there is no context to hold the error, and the next call clears
+ * the error word.
  */
 #define NB_NOALLOC_MAX_N 32768
 nb_status nb_accel_noalloc(int64_t n, const float *x, const float *m, float *a, double G,

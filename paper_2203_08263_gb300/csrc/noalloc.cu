@@ -1,18 +1,19 @@
 // nb_accel_noalloc: the FP32 force sum without any allocation.
 //
 // Some callers cannot allocate device memory at the moment they need
-// forces: code running while a CUDA stream capture is active (cudaMalloc is
-// refused under global capture mode), processes whose device memory is
-// entirely owned by a pooling allocator (a raw cudaMalloc there fails or
-// fragments the pool), and services that must fix their memory footprint
-// when the library loads. For them this entry point needs no context and
-// reserves its working memory once, as a file-scope device array that every
-// GPU loading the library holds until the process exits.
+// forces: processes whose device memory is entirely owned by a pooling
+// allocator (a raw cudaMalloc there fails or fragments the pool), and
+// services that must fix their memory footprint when the library loads. For
+// them this entry point needs no context and reserves its working memory
+// once, as a file-scope device array that every GPU loading the library
+// holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/nbody.h"
 #include "kernels.h"
@@ -43,13 +44,48 @@ static_assert(kMaxIBlocks * 4 <= (int64_t)kCtrBytes, "ticket area too small");
 // Packed bodies, split partials, split tickets and the error word.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// Per-device set-up, done once by the first call on the device: the device
+// address of g_scratch and the SM count. `done` is published with release
+// order after both are written, so a thread that reads it true (acquire)
+// sees them; the first calls of concurrent threads serialise on g_setup_mu.
 struct DeviceSetup {
-    bool done = false;
-    unsigned char *scratch = nullptr;  // device address of g_scratch
+    std::atomic<bool> done{false};
+    unsigned char *scratch = nullptr;
     int num_sms = 0;
 };
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_mu;
+
+bool setup_device(int dev, DeviceSetup &su) {
+    if (su.done.load(std::memory_order_acquire)) return true;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (su.done.load(std::memory_order_relaxed)) return true;
+    // host code cannot use g_scratch's name as an address: ask the runtime
+    // where the array lives on this (current) device
+    void *p = nullptr;
+    int sms = 0;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    su.scratch = static_cast<unsigned char *>(p);
+    su.num_sms = sms;
+    su.done.store(true, std::memory_order_release);
+    return true;
+}
+
+// A caller array: device (or managed) memory of device `dev`, 4-byte aligned.
+bool valid_array(const void *p, int dev) {
+    if (!p || reinterpret_cast<uintptr_t>(p) % 4) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
 
 }  // namespace
 
@@ -60,25 +96,15 @@ extern "C" nb_status nb_accel_noalloc(int64_t n, const float *x, const float *m,
         !((float)(eps * eps) >= 1.17549435e-38f))
         return NB_ERR_INVALID;
     if (n == 0) return NB_OK;
-    if (!x || !m || !a) return NB_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return NB_ERR_CUDA;
     }
+    // argument errors return before anything is launched
+    if (!valid_array(x, dev) || !valid_array(m, dev) || !valid_array(a, dev)) return NB_ERR_INVALID;
     DeviceSetup &su = g_setup[dev];
-    if (!su.done) {
-        // first call on this device: host code cannot use g_scratch's name as
-        // an address, so ask the runtime where the array lives
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess ||
-            cudaDeviceGetAttribute(&su.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return NB_ERR_CUDA;
-        }
-        su.scratch = static_cast<unsigned char *>(p);
-        su.done = true;
-    }
+    if (!setup_device(dev, su)) return NB_ERR_CUDA;
     int cnt = 0;
     const ForceEntry *tab = force_table(kPolF32x2, &cnt);
     const ForceEntry *e = nullptr;

@@ -209,6 +209,30 @@ def test_c3_run_fp64_state(nbm):
     assert rel_l2(to_np(v), vr) <= 1e-6
 
 
+def test_c3_full_size_step_subset(nbm):
+    """Precision form at full size: one FP64-state step of N = 2^20 Plummer
+    (seed 2, eps = 0.05, dt = 5e-4) through nb_step, in the form chosen for
+    the size; the updated v and x of the 4096-body subset against the
+    oracle's update of those bodies (its forces from all N bodies, then the
+    printed half kick and drift; tests/test_oracle_pins.py pins this
+    composition against oracle.step)."""
+    n, G, eps, dt = 1 << 20, 1.0, 0.05, 5e-4
+    s = ics.plummer(n, seed=2)
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    f = torch.float64
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ctx.step(x, v, m)
+    ctx.sync()
+    idx = ics.subset_indices(n, 4096, 2 + 1000)
+    a = oracle.accel(s.x, s.m, G, eps, idx)
+    v_ref = s.v[idx] + a * (dt / 2)
+    x_ref = s.x[idx] + v_ref * dt
+    ev = rel_l2(to_np(v)[idx], v_ref)
+    ex = rel_l2(to_np(x)[idx], x_ref)
+    print(f"C3 one step, 4096 subset: v rel L2 {ev:.3e}, x rel L2 {ex:.3e}")
+    assert ev <= 1e-6 and ex <= 1e-9
+
+
 @pytest.mark.parametrize("form", [0, 1])
 def test_c2_full_size_sampled(nbm, form):
     """Single large system: N=262144 Plummer (seed 1), eps=0.05, FP32;

@@ -95,11 +95,21 @@ def test_adjoint_vs_central_differences(nbm):
             assert abs(ad - fd) <= 1e-4 * max(abs(fd), 1e-12), (which, ad, fd)
 
 
-def test_adjoint_fp32_reported(nbm):
+@pytest.mark.parametrize("form", ["default", "one_sided", "pair_symmetric"])
+def test_adjoint_fp32_vs_fp64_oracle(nbm, form):
+    """The plain FP32 adjoint at the gradient-check size (N = 64, T = 20,
+    k = 20) against the FP64 oracle's gradient: within 1e-6 in the forms
+    nb_run and nb_adjoint choose for this size (the bench reports the same
+    error), and within 2e-6 with the graph path's one-sided or
+    pair-symmetric kernels pinned."""
     s, xstar, G, eps, dt, T = _problem()
     n = s.n
     f = torch.float32
     ctx = nbm.Context(G, eps, dt)
+    if form != "default":
+        ctx.debug_set(nbm.NB_DBG_RUN_PATH, 1)
+        ctx.debug_set(nbm.NB_DBG_FORM, 1 if form == "one_sided" else 256)
+        ctx.debug_set(nbm.NB_DBG_VJP_FORM, 1 if form == "one_sided" else 256)
     x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
     ck = torch.empty((T // 20 + 1, n, 6), dtype=f, device=DEV)
     ctx.run(x, v, m, T, ckpt=ck, ckpt_every=20)
@@ -108,8 +118,8 @@ def test_adjoint_fp32_reported(nbm):
     xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
     rx, rv, rm = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
     errs = [rel_l2(to_np(gx), rx), rel_l2(to_np(gv), rv), rel_l2(to_np(gm), rm)]
-    print("adjoint fp32: %s" % ["%.2e" % e for e in errs])
-    assert max(errs) <= 1e-3
+    print("adjoint fp32 (%s): %s" % (form, ["%.2e" % e for e in errs]))
+    assert max(errs) <= (1e-6 if form == "default" else 2e-6)
 
 
 def test_autograd_function_gradients(nbm):
@@ -192,3 +202,38 @@ def test_c5_full_size_directional_derivatives(nbm):
         err = rel_l2(to_np(a), to_np(b))
         print(f"C5 FP32 vs precision-form gradient: {err:.2e}")
         assert err <= 1e-3
+
+
+def test_c5_size_directional_derivatives_vs_oracle_forward(nbm):
+    """Adjoint at the C5 size, N = 16384 (cube, seed 4), against the FP64
+    oracle rather than the library's own forward: directional derivatives of
+    the precision-form gradient against central differences of the oracle's
+    run, over T = 40 steps with a checkpoint every 20 (two recomputed
+    segments; the oracle's FP64 run of all 16384 bodies takes about a second
+    per 20 steps on the host)."""
+    n, T, k, G, eps, dt = 16384, 40, 20, 1.0, 0.01, 1e-3
+    s = ics.cube(n, seed=4, masses="equal")
+    xstar = ics.targets(n, seed=4)
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - _t(xstar, f))
+    grads = {w: to_np(g) for w, g in zip("xvm", ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT)))}
+
+    def loss(x0, v0, m0):
+        xT, _ = oracle.run(x0, v0, m0, G, eps, dt, T)
+        return float(((xT - xstar) ** 2).sum())
+
+    rng = np.random.default_rng(6)
+    base = {"x": s.x, "v": s.v, "m": s.m}
+    for which, h in (("x", 1e-5), ("v", 1e-4), ("m", 1e-8)):
+        d = rng.normal(size=base[which].shape)
+        plus, minus = dict(base), dict(base)
+        plus[which] = base[which] + h * d
+        minus[which] = base[which] - h * d
+        fd = (loss(plus["x"], plus["v"], plus["m"]) - loss(minus["x"], minus["v"], minus["m"])) / (2 * h)
+        ad = float((grads[which] * d).sum())
+        print(f"C5 size {which}: adjoint {ad:.8e} oracle central difference {fd:.8e}")
+        assert abs(ad - fd) <= 1e-4 * abs(fd)

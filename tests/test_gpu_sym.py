@@ -287,3 +287,24 @@ def test_sym_compensated_run_matches_oracle(nbm, scheme):
     xr, vr = oracle.run(s.x, s.v, s.m, G, eps, dt, T, scheme=scheme)
     assert rel_l2(to_np(x), xr) <= 1e-9
     assert rel_l2(to_np(v), vr) <= 1e-6
+
+
+@pytest.mark.parametrize("block", [256, 512, 1024])
+@pytest.mark.parametrize("n", [65536, 262144])
+def test_sym_compensated_close_encounters(nbm, block, n):
+    """The precision form's 1e-6 bound on close-encounter-heavy input: a
+    uniform cube with eps = 0.01 (about 0.03 to 0.14 neighbours per body inside
+    eps at these sizes), where each block-pair partial is an FP32 sum of up to
+    the block's length of terms, some of them near the largest a pair can
+    give (0.385 m / eps^2). Element-wise against the FP64 oracle on 1024
+    sampled bodies, each block size pinned."""
+    G, eps = 1.0, 0.01
+    s = ics.cube(n, seed=17, masses="equal")
+    ctx = nbm.Context(G, eps, 5e-4, precision="comp")
+    ctx.debug_set(nbm.NB_DBG_FORM, block)
+    assert ctx.get_config(n)["form"] == "compensated_pair_symmetric"
+    a = to_np(ctx.accel(_t(s.x, torch.float64), _t(s.m, torch.float64)))
+    idx = ics.subset_indices(n, 1024, 17 + block)
+    err = rel_l2(a[idx], oracle.accel(s.x, s.m, G, eps, idx))
+    print(f"precision form, cube eps=0.01, n={n}, block {block}: rel L2 {err:.3e}")
+    assert err <= 1e-6

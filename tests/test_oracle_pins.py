@@ -76,6 +76,37 @@ def test_step_matches_decimal_update():
     assert _rel(x1, old_v_x) > 1e-9
 
 
+def test_accel_subset_rows_equal_full_rows():
+    """The i-subset branch of oracle.accel (the reference of every full-size
+    GPU test) returns exactly the rows of the full sum: unsorted and repeated
+    indices, both ends, a strided subset and the empty subset."""
+    s = ics.plummer(700, seed=21)
+    G, eps = 1.0, 0.05
+    full = oracle.accel(s.x, s.m, G, eps)
+    for idx in (np.array([0, 699, 350, 350, 1]), np.arange(700)[::-7], np.zeros(0, np.int64)):
+        sub = oracle.accel(s.x, s.m, G, eps, idx)
+        assert sub.shape == (len(idx), 3)
+        assert np.array_equal(sub, full[idx])
+    with pytest.raises(IndexError):
+        oracle.accel(s.x, s.m, G, eps, np.array([700]))
+
+
+def test_step_is_subset_accel_then_printed_update():
+    """oracle.step on the rows of a subset is bit for bit the subset's
+    oracle.accel followed by the printed half kick and drift with the new v
+    (the composition that the full-size GPU step test uses as its
+    reference)."""
+    s = ics.cube(300, seed=22)
+    G, eps, dt = 1.0, 0.01, 5e-4
+    x1, v1 = oracle.step(s.x, s.v, s.m, G, eps, dt)
+    idx = np.array([3, 0, 299, 150, 77])
+    a = oracle.accel(s.x, s.m, G, eps, idx)
+    v_ref = s.v[idx] + a * (dt / 2)
+    x_ref = s.x[idx] + v_ref * dt
+    assert np.array_equal(v1[idx], v_ref)
+    assert np.array_equal(x1[idx], x_ref)
+
+
 # ------------------------------------------------------------- closed forms
 
 def test_two_body_closed_form_and_direction():
