@@ -393,18 +393,24 @@ __global__ void __launch_bounds__(NT, (batched_min_blocks<NT, RMAX>())) batched_
     }
 }
 
+// Pack every system into buffer 0 with zero-mass padding to whole j-tiles,
+// and zero the padding of buffer 1 too: the steps' epilogues repack real
+// bodies only, and the scratch may hold another plan's bodies (a tuning run
+// with another j-tile, or other sizes) where this plan pads.
 template <class TS>
 __global__ void batched_pack_kernel(const int64_t *off, const int64_t *poff, int jt,
-                                    const TS *x, const TS *m, float4 *xm) {
+                                    const TS *x, const TS *m, float4 *xm, float4 *xm1) {
     const int s = blockIdx.x;
     const int64_t b0 = off[s], n = off[s + 1] - b0, p0 = poff[s];
     const int64_t npad = (n + jt - 1) / jt * jt;
     for (int64_t i = threadIdx.x; i < npad; i += blockDim.x) {
-        if (i < n)
+        if (i < n) {
             pair_put(xm + p0, i, (float)x[3 * (b0 + i)], (float)x[3 * (b0 + i) + 1],
                      (float)x[3 * (b0 + i) + 2], (float)m[b0 + i]);
-        else
+        } else {
             pair_put(xm + p0, i, 0.f, 0.f, 0.f, 0.f);
+            pair_put(xm1 + p0, i, 0.f, 0.f, 0.f, 0.f);
+        }
     }
 }
 
@@ -649,10 +655,10 @@ cudaError_t batched_enqueue(const BatchPlan &p, void *scratch, void *x, void *v,
     if (e != cudaSuccess) return e;
     if (p.f64)
         batched_pack_kernel<double><<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, (const double *)x,
-                                                            (const double *)m, a.xm0);
+                                                            (const double *)m, a.xm0, a.xm1);
     else
         batched_pack_kernel<float><<<p.nsys, 256, 0, st>>>(a.off, a.poff, p.jt, (const float *)x,
-                                                           (const float *)m, a.xm0);
+                                                           (const float *)m, a.xm0, a.xm1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;

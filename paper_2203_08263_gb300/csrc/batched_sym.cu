@@ -15,6 +15,11 @@
 // numbers, so the oldest unfinished item is always ready and the queue always
 // makes progress.
 //
+// A diagonal item (gi == gj) evaluates each unordered pair of its group about
+// once (pair_item_diag: the off-diagonal 32 x 64 squares of the group take
+// both sides of each pair, the 64 x 64 squares on the diagonal every ordered
+// pair from the i side), 20 of the 32 squares an off-diagonal item evaluates.
+//
 // The unit of work is a warp: each warp of the persistent grid takes item
 // numbers from one atomic counter, holds up to kHoldW of them (one by
 // default) and runs the lowest-numbered ready one; it takes the next number
@@ -102,7 +107,6 @@ __device__ __forceinline__ void pair_item(const SymBatchArgs &a, const float4 *s
         mi[r] = dup(pget_cg(src, i, 3));
         ax[r] = ay[r] = az[r] = f2(0.f, 0.f);
     }
-    const bool diag = gi == gj;
     for (int ch = 0; ch < kGrp / 64; ++ch) {
         const int64_t q = (int64_t)gj * (kGrp / 2) + ch * 32 + lane;  // this lane's record
         const float4 r0 = __ldcg(src + 2 * q), r1 = __ldcg(src + 2 * q + 1);
@@ -137,7 +141,7 @@ __device__ __forceinline__ void pair_item(const SymBatchArgs &a, const float4 *s
             by = shfl2(by, next);
             bz = shfl2(bz, next);
         }
-        if (!diag) {  // j side: row gi of the partials, bodies of group gj
+        {  // j side: row gi of the partials, bodies of group gj
             float *p = P + (int64_t)gi * 3 * npad + (int64_t)gj * kGrp + ch * 64 + 2 * lane;
             __stcg(reinterpret_cast<float2 *>(p), f2(-bx.x, -bx.y));
             __stcg(reinterpret_cast<float2 *>(p + npad), f2(-by.x, -by.y));
@@ -151,6 +155,99 @@ __device__ __forceinline__ void pair_item(const SymBatchArgs &a, const float4 *s
         __stcg(p + npad + 32 * r, ay[r].x + ay[r].y);
         __stcg(p + 2 * npad + 32 * r, az[r].x + az[r].y);
     }
+}
+
+// The diagonal item (gi == gj) with each unordered pair evaluated about
+// once: in chunk CH (j-bodies 64 CH ... 64 CH + 63) the lane's i-bodies of
+// sub-block r (bodies 32 r + lane) take both sides of the pair for r < 2 CH
+// (all those j-bodies are higher), the i side only for r = 2 CH, 2 CH + 1
+// (the 64 x 64 block on the diagonal, every ordered pair; the own pair adds
+// 0), and nothing for r > 2 CH + 1 (those pairs are the mirror images of
+// ones already taken). The j-side sums of a chunk wait in `stage` and join
+// the i-side sums of the same bodies before the one partial of row gi is
+// stored.
+template <int CH>
+__device__ __forceinline__ void diag_chunk(const float4 *src, int gi, int lane, float2 eps2,
+                                           const float2 (&nx)[kGR], const float2 (&ny)[kGR],
+                                           const float2 (&nz)[kGR], const float2 (&mi)[kGR],
+                                           float2 (&ax)[kGR], float2 (&ay)[kGR], float2 (&az)[kGR],
+                                           float *stage) {
+    const int next = (lane + 1) & 31;
+    const int64_t q = (int64_t)gi * (kGrp / 2) + CH * 32 + lane;
+    const float4 r0 = __ldcg(src + 2 * q), r1 = __ldcg(src + 2 * q + 1);
+    float2 xj = f2(r0.x, r0.y), yj = f2(r0.z, r0.w), zj = f2(r1.x, r1.y), mj = f2(r1.z, r1.w);
+    float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
+#pragma unroll 1
+    for (int round = 0; round < 32; ++round) {
+#pragma unroll
+        for (int r = 0; r < kGR; ++r) {
+            if (r > 2 * CH + 1) continue;
+            const float2 dx = __fadd2_rn(xj, nx[r]);
+            const float2 dy = __fadd2_rn(yj, ny[r]);
+            const float2 dz = __fadd2_rn(zj, nz[r]);
+            float2 s = __ffma2_rn(dx, dx, eps2);
+            s = __ffma2_rn(dy, dy, s);
+            s = __ffma2_rn(dz, dz, s);
+            const float2 y = rsqrt_mufu2(s);
+            const float2 y3 = __fmul2_rn(__fmul2_rn(y, y), y);
+            const float2 wi = __fmul2_rn(mj, y3);
+            ax[r] = __ffma2_rn(wi, dx, ax[r]);
+            ay[r] = __ffma2_rn(wi, dy, ay[r]);
+            az[r] = __ffma2_rn(wi, dz, az[r]);
+            if (r < 2 * CH) {
+                const float2 wj = __fmul2_rn(mi[r], y3);
+                bx = __ffma2_rn(wj, dx, bx);
+                by = __ffma2_rn(wj, dy, by);
+                bz = __ffma2_rn(wj, dz, bz);
+            }
+        }
+        xj = shfl2(xj, next);
+        yj = shfl2(yj, next);
+        zj = shfl2(zj, next);
+        mj = shfl2(mj, next);
+        if (CH > 0) {
+            bx = shfl2(bx, next);
+            by = shfl2(by, next);
+            bz = shfl2(bz, next);
+        }
+    }
+    const int b = CH * 64 + 2 * lane;
+    stage[b] = -bx.x;
+    stage[b + 1] = -bx.y;
+    stage[kGrp + b] = -by.x;
+    stage[kGrp + b + 1] = -by.y;
+    stage[2 * kGrp + b] = -bz.x;
+    stage[2 * kGrp + b + 1] = -bz.y;
+}
+
+__device__ __forceinline__ void pair_item_diag(const float4 *src, float *P, int64_t npad, int gi,
+                                               int lane, float2 eps2, float *stage) {
+    float2 nx[kGR], ny[kGR], nz[kGR], mi[kGR], ax[kGR], ay[kGR], az[kGR];
+    const int64_t ib = (int64_t)gi * kGrp + lane;
+#pragma unroll
+    for (int r = 0; r < kGR; ++r) {
+        const int64_t i = ib + 32 * r;
+        nx[r] = dup(-pget_cg(src, i, 0));
+        ny[r] = dup(-pget_cg(src, i, 1));
+        nz[r] = dup(-pget_cg(src, i, 2));
+        mi[r] = dup(pget_cg(src, i, 3));
+        ax[r] = ay[r] = az[r] = f2(0.f, 0.f);
+    }
+    static_assert(kGrp == 256 && kGR == 8, "the diagonal schedule assumes 4 chunks of 64 bodies");
+    diag_chunk<0>(src, gi, lane, eps2, nx, ny, nz, mi, ax, ay, az, stage);
+    diag_chunk<1>(src, gi, lane, eps2, nx, ny, nz, mi, ax, ay, az, stage);
+    diag_chunk<2>(src, gi, lane, eps2, nx, ny, nz, mi, ax, ay, az, stage);
+    diag_chunk<3>(src, gi, lane, eps2, nx, ny, nz, mi, ax, ay, az, stage);
+    __syncwarp();
+    float *p = P + (int64_t)gi * 3 * npad + ib;  // row gi, bodies of group gi
+#pragma unroll
+    for (int r = 0; r < kGR; ++r) {
+        const int b = lane + 32 * r;
+        __stcg(p + 32 * r, (ax[r].x + ax[r].y) + stage[b]);
+        __stcg(p + npad + 32 * r, (ay[r].x + ay[r].y) + stage[kGrp + b]);
+        __stcg(p + 2 * npad + 32 * r, (az[r].x + az[r].y) + stage[2 * kGrp + b]);
+    }
+    __syncwarp();  // the stage is free for the warp's next item
 }
 
 // Group g's bodies: partials in group order, then the update of step t.
@@ -256,6 +353,7 @@ __global__ void __launch_bounds__(kSymWarps * 32, F64 ? 3 : NB_SYMB_MINB) batche
         int nheld, exhausted;
     };
     __shared__ WarpQueue s_q[kSymWarps];
+    __shared__ float s_stage[kSymWarps][3 * kGrp];  // a diagonal item's j-side sums
     WarpQueue &Q = s_q[threadIdx.x >> 5];
     if (lane == 0) {
         for (int k = 0; k < kHoldW; ++k) {
@@ -371,7 +469,11 @@ __global__ void __launch_bounds__(kSymWarps * 32, F64 ? 3 : NB_SYMB_MINB) batche
         if (!ab) {
             if (it.w == 0) {
                 const float4 *src = ((t & 1) ? a.xm1 : a.xm0) + a.poff[s];
-                pair_item(a, src, a.part + a.pofs[s], (int64_t)a.ng[s] * kGrp, it.y, it.z, lane);
+                if (it.y == it.z)
+                    pair_item_diag(src, a.part + a.pofs[s], (int64_t)a.ng[s] * kGrp, it.y, lane,
+                                   dup(a.eps2), s_stage[threadIdx.x >> 5]);
+                else
+                    pair_item(a, src, a.part + a.pofs[s], (int64_t)a.ng[s] * kGrp, it.y, it.z, lane);
             } else {
                 epilogue_item<F64>(a, s, it.y, t, lane);
             }
@@ -453,7 +555,8 @@ double batched_sym_work_ratio(const std::vector<int64_t> &off) {
     for (size_t s = 0; s + 1 < off.size(); ++s) {
         const int64_t n = off[s + 1] - off[s];
         const int64_t g = (n + kGrp - 1) / kGrp;
-        sym += 16.0 * (double)(g * (g + 1) / 2) * kGrp * kGrp;
+        // a diagonal item evaluates 20 of the 32 (sub-block, chunk) squares
+        sym += 16.0 * ((double)(g * (g - 1) / 2) + 0.625 * (double)g) * kGrp * kGrp;
         one += 12.0 * (double)n * (double)n;
     }
     return one > 0 ? sym / one : 1e30;

@@ -52,8 +52,16 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 }
 
 // Forces.
+#ifndef NB_SYM_ACCEL_REC_SMEM
+#define NB_SYM_ACCEL_REC_SMEM 0  // records by shuffle: 3.987e12 against 3.962e12 staged (N = 262144)
+#endif
+#ifndef NB_SYM_VJP_REC_SMEM
+#define NB_SYM_VJP_REC_SMEM 1  // records staged: 2.6 against 2.8 ms at N = 65536, 46.9 against 49.2 ms per C5 adjoint
+#endif
+
 struct SymAccel {
     static constexpr int R = kSymR;
+    static constexpr bool REC_SMEM = NB_SYM_ACCEL_REC_SMEM;  // chunk records staged in shared memory
     static constexpr int REGS = 128;  // register target: 4 CTAs of 4 warps per SM (126 used)
     static constexpr int NACC = 3;      // a_x, a_y, a_z
     static constexpr int REC_F4 = 2;    // {x0,x1,y0,y1} {z0,z1,m0,m1}
@@ -81,6 +89,14 @@ struct SymAccel {
         j.y = shfl2(j.y, src);
         j.z = shfl2(j.z, src);
         j.m = shfl2(j.m, src);
+    }
+    // record q of a chunk staged in shared memory as [REC_F4][32] float4
+    __device__ static void load_j_smem(const float4 *rb, int q, J &j) {
+        const float4 r0 = rb[q], r1 = rb[32 + q];
+        j.x = f2(r0.x, r0.y);
+        j.y = f2(r0.z, r0.w);
+        j.z = f2(r1.x, r1.y);
+        j.m = f2(r1.z, r1.w);
     }
     template <bool MASK>
     __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
@@ -137,6 +153,7 @@ struct SymComp : SymAccel {
 #endif
 struct SymVjp {
     static constexpr int R = kSymVjpR;
+    static constexpr bool REC_SMEM = NB_SYM_VJP_REC_SMEM;
     static constexpr int REGS = NB_SYM_VJP_REGS;  // register target
     static constexpr int NACC = 8;
     static constexpr int REC_F4 = 4;
@@ -174,6 +191,17 @@ struct SymVjp {
         j.ax = shfl2(j.ax, src);
         j.ay = shfl2(j.ay, src);
         j.az = shfl2(j.az, src);
+    }
+    __device__ static void load_j_smem(const float4 *rb, int q, J &j) {
+        const float4 r0 = rb[q], r1 = rb[32 + q], r2 = rb[64 + q];
+        const float2 r3 = *reinterpret_cast<const float2 *>(rb + 96 + q);
+        j.x = f2(r0.x, r0.y);
+        j.y = f2(r0.z, r0.w);
+        j.z = f2(r1.x, r1.y);
+        j.m = f2(r1.z, r1.w);
+        j.ax = f2(r2.x, r2.y);
+        j.ay = f2(r2.z, r2.w);
+        j.az = r3;
     }
     template <bool MASK>
     __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
@@ -269,6 +297,34 @@ __device__ __forceinline__ void chunk_rounds(typename S::J &sj, const typename S
     }
 }
 
+// The same 32 rounds with the chunk's records staged in shared memory
+// (rb: [REC_F4][32] float4): at round r lane l reads record (l + r) mod 32
+// itself, so only the running j-side sums travel between lanes.
+template <class S, bool MASK>
+__device__ __forceinline__ void chunk_rounds_smem(const float4 *rb, const typename S::I (&si)[S::R],
+                                                  float2 (&ai)[S::R][S::NACC], float2 (&aj)[S::NACC],
+                                                  const typename S::C &c, int l, int next, int i_base,
+                                                  int j_base) {
+#pragma unroll kRoundUnroll
+    for (int round = 0; round < 32; ++round) {
+        const int q = (l + round) & 31;
+        const int j0 = j_base + 2 * q;
+        typename S::J sj;
+        S::load_j_smem(rb, q, sj);
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) {
+            float2 keep = f2(1.f, 1.f);
+            if constexpr (MASK) {
+                const int i = i_base + 32 * r;
+                keep = f2(i == j0 ? 0.f : 1.f, i == j0 + 1 ? 0.f : 1.f);
+            }
+            S::template pair<MASK>(sj, si[r], ai[r], aj, c, keep);
+        }
+#pragma unroll
+        for (int k = 0; k < S::NACC; ++k) aj[k] = shfl2(aj[k], next);
+    }
+}
+
 // Resident CTAs per SM that keep a policy's registers at its target (the
 // compiler's own choice without a bound; a bound of 1 CTA let it take 210 for
 // the VJP).
@@ -303,17 +359,43 @@ __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(c
     }
     const bool diag = bi == bj;
     float *mine = acc_j + w * NA * B;
+    // S::REC_SMEM: this warp's two record buffers, [2][REC_F4][32] float4
+    // after acc_j; chunk ch + 1 is copied while chunk ch is evaluated
+    float4 *rbw = reinterpret_cast<float4 *>(acc_j + W * NA * B) + w * 2 * S::REC_F4 * 32;
+    auto issue = [&](int ch) {
+        const float4 *src = a.src + ((int64_t)bj * (B / 2) + ch * 32 + l) * S::REC_F4;
+        float4 *dst = rbw + (ch & 1) * S::REC_F4 * 32 + l;
+#pragma unroll
+        for (int f = 0; f < S::REC_F4; ++f) cp_async16(dst + f * 32, src + f);
+        cp_async_commit();
+    };
+    if constexpr (S::REC_SMEM) issue(0);
     for (int ch = 0; ch < B / 64; ++ch) {
-        const int64_t q = (int64_t)bj * (B / 2) + ch * 32 + l;  // this lane's record
-        typename S::J sj;
-        S::load_j(a.src + q * S::REC_F4, sj);
         float2 aj[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) aj[k] = f2(0.f, 0.f);
-        if (S::SELF_MASK && diag)
-            chunk_rounds<S, true>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
-        else
-            chunk_rounds<S, false>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
+        if constexpr (S::REC_SMEM) {
+            if (ch + 1 < B / 64)
+                issue(ch + 1);
+            else
+                cp_async_commit();  // an empty group keeps "all but the newest" meaning chunk ch
+            cp_async_wait<1>();
+            __syncwarp();
+            const float4 *rb = rbw + (ch & 1) * S::REC_F4 * 32;
+            if (S::SELF_MASK && diag)
+                chunk_rounds_smem<S, true>(rb, si, ai, aj, c, l, next, i_base, ch * 64);
+            else
+                chunk_rounds_smem<S, false>(rb, si, ai, aj, c, l, next, i_base, ch * 64);
+            __syncwarp();  // every lane is done with buffer ch & 1 before chunk ch + 2 refills it
+        } else {
+            const int64_t q = (int64_t)bj * (B / 2) + ch * 32 + l;  // this lane's record
+            typename S::J sj;
+            S::load_j(a.src + q * S::REC_F4, sj);
+            if (S::SELF_MASK && diag)
+                chunk_rounds<S, true>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
+            else
+                chunk_rounds<S, false>(sj, si, ai, aj, c, l, next, i_base, ch * 64);
+        }
         if (!diag) {
             const int kb = ch * 64 + 2 * l;
 #pragma unroll
@@ -414,7 +496,8 @@ cudaError_t launch_ex(const void *fn, dim3 grid, dim3 block, size_t smem, bool p
 
 template <class S, int W>
 constexpr size_t sym_smem() {
-    return (size_t)W * S::NACC * (W * 32 * S::R) * 4;
+    return (size_t)W * S::NACC * (W * 32 * S::R) * 4 +
+           (S::REC_SMEM ? (size_t)W * 2 * S::REC_F4 * 32 * 16 : 0);
 }
 
 template <class S, int W>

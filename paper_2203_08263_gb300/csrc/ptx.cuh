@@ -73,6 +73,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through L2 (cp.async.cg),
+// counted in the issuing thread's current group; dst and src 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most `pending` of this thread's committed groups are in flight.
+template <int pending>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(pending) : "memory");
+}
+
 // MUFU reciprocal square root without the denormal-input path (PTX
 // rsqrt.approx.ftz.f32). Every argument in this library is >= eps^2, a normal
 // float (the context rejects smaller eps).

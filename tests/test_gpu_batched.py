@@ -208,6 +208,52 @@ def test_batched_precision_form_tuned_and_pinned(nbm):
         assert rel_l2(to_np(xt)[a:b], xr) <= 1e-9
 
 
+@pytest.mark.parametrize("form", ["one_sided", "pair_symmetric"])
+def test_batched_padding_not_stale_after_other_plans(nbm, form):
+    """Odd-sized systems read the padding half of their last pair record at
+    every step. A context whose scratch last served other plans (a tuning run
+    with another j-tile does exactly this) holds other bodies where this plan
+    pads; the pack must clear the padding of both position buffers. The
+    precision form's tolerances (1e-9 in x, 1e-6 in v after 4 steps) see one
+    stale body of mass 1/N in a system."""
+    sizes = [65, 129, 301, 777, 1023, 1]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rng = np.random.default_rng(21)
+    x = rng.uniform(-1, 1, (off[-1], 3))
+    v = rng.uniform(-0.1, 0.1, (off[-1], 3))
+    m = np.concatenate([np.full(n, 1.0 / n) for n in sizes])
+    ctx = nbm.Context(1.0, 0.01, 1e-3, precision="comp")
+    offt = torch.tensor(off, dtype=torch.int64)
+    f = torch.float64
+    # other plans first: two one-sided j-tiles and the other form, on shifted bodies
+    for nt, r, jt in ((256, 1, 128), (128, 2, 64)):
+        ctx.set_batched_config(offt, nt, r, jt)
+        xs, vs, ms = (torch.tensor(a + 0.3, dtype=f, device=DEV) for a in (x, v, m))
+        ctx.run_batched(offt, xs, vs, ms, 3)
+    ctx.set_batched_config(offt, 0, 0, 0)
+    ctx.set_batched_form(offt, "pair_symmetric" if form == "one_sided" else "one_sided")
+    xs, vs, ms = (torch.tensor(a + 0.3, dtype=f, device=DEV) for a in (x, v, m))
+    ctx.run_batched(offt, xs, vs, ms, 3)
+    if form == "one_sided":
+        ctx.set_batched_form(offt, None)
+        ctx.set_batched_config(offt, 128, 4, 128)
+    else:
+        ctx.set_batched_form(offt, "pair_symmetric")
+    assert ctx.get_batched_config(offt)["form"] == form
+    xt, vt, mt = (torch.tensor(a, dtype=f, device=DEV) for a in (x, v, m))
+    ctx.run_batched(offt, xt, vt, mt, 4)
+    ctx.sync()
+    gx, gv = to_np(xt), to_np(vt)
+    for s_ in range(len(sizes)):
+        a, b = off[s_], off[s_ + 1]
+        xr, vr = oracle.run(x[a:b], v[a:b], m[a:b], 1.0, 0.01, 1e-3, 4)
+        if sizes[s_] == 1:
+            assert np.array_equal(gv[a:b], v[a:b])
+            continue
+        assert rel_l2(gx[a:b], xr) <= 1e-9, s_
+        assert rel_l2(gv[a:b], vr) <= 1e-6, s_
+
+
 # ------------------------------------------------- pair-symmetric form
 
 SYM_SIZES = [1, 0, 2, 3, 65, 130, 0, 255, 256, 257, 33, 300, 513, 1000, 2047]
