@@ -337,7 +337,14 @@ typedef enum {
     /* FP32 VJP form (nb_vjp, nb_adjoint): 0 = chosen per size (default),
      * 1 = one-sided only, 256 or 512 = the pair-symmetric kernel with blocks
      * of that many bodies at every size. */
-    NB_DBG_VJP_FORM = 6
+    NB_DBG_VJP_FORM = 6,
+    /* Pair-symmetric launches (forces, precision form, VJP): 0 = chosen per
+     * size (default: one launch over all block pairs up to 2 GiB of
+     * partials, above that one launch per tile of w x w block pairs with a
+     * running sum of the partials, two tile buffers of at most 64 MiB), -1 =
+     * one launch always, w > 0 = tiles of w blocks whenever that makes more
+     * than one tile. Results are bit-identical either way. */
+    NB_DBG_SYM_TILE = 7
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 

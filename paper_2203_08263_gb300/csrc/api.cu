@@ -264,6 +264,13 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         clear_graphs(ctx);
         return NB_OK;
     }
+    if (key == NB_DBG_SYM_TILE) {
+        if (value < -1 || value > (1 << 20))
+            return fail(ctx, NB_ERR_INVALID, "tile side must be -1, 0 or a block count");
+        ctx->sym_tile = (int)value;
+        clear_graphs(ctx);
+        return NB_OK;
+    }
     if (key == NB_DBG_STALL_PRODUCER) {
         if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
         ctx->debug = value ? (ctx->debug | kDbgStallProducer) : (ctx->debug & ~kDbgStallProducer);

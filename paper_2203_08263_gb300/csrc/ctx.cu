@@ -194,12 +194,10 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     int nt = 128, r = 1, jt = 64;
     if ((pol == kPolF32x2 || pol == kPolComp) && allow_sym && n >= 16384) {
         // each unordered pair once, blocks of 1024 bodies from 2^17 up (enough
-        // block pairs to fill the GPU), 512 below; the one-sided policy above
-        // the partial-buffer cap
+        // block pairs to fill the GPU), 512 below
         const int snt = n >= 131072 ? 128 : 64;
-        const int64_t b = (int64_t)snt * kSymR, np = round_up(n, b);
-        if ((size_t)(np / b) * 3 * (size_t)np * 4 <= kSymMaxPartBytes)
-            return Shape{pol == kPolComp ? kPolSymComp : kPolSym, snt, kSymR, 1, (int)b};
+        const int64_t b = (int64_t)snt * kSymR;
+        return Shape{pol == kPolComp ? kPolSymComp : kPolSym, snt, kSymR, 1, (int)b};
     }
     if (pol == kPolF32x2) {
         if (n >= 32768) { r = 4; jt = 128; }
@@ -216,11 +214,8 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     } else if (pol == kPolVjp && allow_sym && n >= 8192) {
         // each unordered pair once: blocks of 256 bodies below 2^16, 512 from there
         const int snt = n >= 65536 ? 128 : 64;
-        const int64_t b = (int64_t)snt * kSymVjpR, np = round_up(n, b);
-        if ((size_t)(np / b) * 8 * (size_t)np * 4 <= kSymMaxPartBytes)
-            return Shape{kPolVjpSym, snt, kSymVjpR, 1, (int)b};
-        r = 2;
-        jt = 128;
+        const int64_t b = (int64_t)snt * kSymVjpR;
+        return Shape{kPolVjpSym, snt, kSymVjpR, 1, (int)b};
     } else {  // VJP (the precision form's R = 2 instance spills at the 128-register cap)
         r = (n >= 8192 && pol == kPolVjp) ? 2 : 1;
         if (n >= 4096) jt = 128;
@@ -280,10 +275,25 @@ nb_status make_plan(nb_ctx *ctx, const Shape &s, int64_t n, Plan *p) {
         p->npad = round_up(std::max<int64_t>(n, 1), b);
         p->iblocks = (int)(p->npad / b);
         p->ntiles = p->iblocks;
-        p->part_bytes = (size_t)p->iblocks * sym_sums(s.pol) * (size_t)p->npad * 4;
-        if (p->part_bytes > kSymMaxPartBytes)
-            return fail(ctx, NB_ERR_UNSUPPORTED, "pair-symmetric partials for %lld bodies exceed %zu bytes",
-                        (long long)n, kSymMaxPartBytes);
+        const int na = sym_sums(s.pol);
+        p->part_bytes = (size_t)p->iblocks * na * (size_t)p->npad * 4;
+        // above kSymTileAbove bytes of partials for one launch, launches by
+        // tiles of w x w block pairs: two tile buffers (within
+        // kSymTileBufBytes, about four waves of CTAs per tile) and the
+        // running sums [2][sums][npad]
+        int w = ctx->sym_tile > 0 ? ctx->sym_tile : 0;
+        if (ctx->sym_tile == 0 && p->part_bytes > kSymTileAbove) {
+            const int64_t slots = (int64_t)std::max(p->e->occupancy((int)b), 1) * ctx->num_sms;
+            const double slot_bytes = 2.0 * na * (double)b * 4;
+            const int w_waves = (int)std::sqrt(4.0 * (double)slots);
+            const int w_buf = (int)std::sqrt((double)kSymTileBufBytes / (2.0 * slot_bytes));
+            w = std::max(1, std::min(w_waves, w_buf));
+        }
+        if (w > 0 && w < p->iblocks) {
+            p->tile_w = w;
+            p->ntile = sym_tile_count(p->iblocks, w);
+            p->part_bytes = 2 * (size_t)w * w * 2 * na * (size_t)b * 4 + 2 * (size_t)na * p->npad * 4;
+        }
         return NB_OK;
     }
     p->npad = round_up(std::max<int64_t>(n, 1), kPadBodies);
@@ -319,12 +329,15 @@ ForceArgs base_args(nb_ctx *ctx, const Plan &p, int64_t n, const float4 *src) {
     a.err = ctx->err_word;
     a.timeout_ns = ctx->timeout_ns;
     a.debug = ctx->debug;
+    a.tile_w = p.tile_w;
+    a.ntile = p.ntile;
     return a;
 }
 
 nb_status launch_force(nb_ctx *ctx, const Plan &p, const ForceArgs &a, cudaStream_t st) {
     NB_CUDA(p.e->launch(p.s.jt, a, st));
-    ctx->launches += pol_is_sym(p.s.pol) ? 2 : 1;  // the pair kernel and its fixed-order sum
+    // the pair kernel (one per tile) and its fixed-order sum with the epilogue
+    ctx->launches += pol_is_sym(p.s.pol) ? (p.ntile > 0 ? p.ntile + 1 : 2) : 1;
     return NB_OK;
 }
 

@@ -56,6 +56,7 @@ struct nb_ctx {
     int run_path = 0;  // nb_run: 0 chosen per size, 1 graph of force launches, 2 one cluster, 3 grid
     int form_pin = 0;  // FP32 forward: 0 chosen per size, 1 one-sided only, 512/1024 pair-symmetric blocks
     int vjp_form_pin = 0;  // FP32 VJP: 0 chosen per size, 1 one-sided only, 256/512 pair-symmetric blocks
+    int sym_tile = 0;      // pair-symmetric tiles: 0 chosen per size, -1 never, w > 0 tiles of w blocks
     std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;
@@ -94,6 +95,7 @@ struct Plan {
     int64_t npad;
     int iblocks, ntiles;
     size_t part_bytes;
+    int tile_w = 0, ntile = 0;  // pair-symmetric forms launched by tiles of tile_w blocks (0: one launch)
 };
 
 // Record a formatted error message on ctx and return s.

@@ -102,6 +102,13 @@ struct ForceArgs {
     const void *mass;     // [n] state-type masses (adjoint epilogue)
     int debug;            // bit 0: the producer issues no copies (timeout tests)
     int pdl;              // host: launched as a programmatic dependent of the previous kernel
+    // pair-symmetric kernels launched tile by tile (csrc/k_sym.cu): the tile
+    // side in blocks (0: one launch over all block pairs), this launch's
+    // tile and the number of tiles; `part` then holds two tile buffers and
+    // the bodies' running sums
+    int tile_w;
+    int tile;
+    int ntile;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -71,6 +71,11 @@ struct SymAccel {
     struct J { float2 x, y, z, m; };
     struct C { float2 eps2; };
     __device__ static void consts(const ForceArgs &a, C &c) { c.eps2 = dup(a.eps2); }
+    // Positions are read-only for the whole step (the step's epilogue writes
+    // the other buffer). A tile launch other than the first of its step does
+    // not wait for the grid that wrote them, but that grid completed before
+    // the first tile's CTAs passed their wait and so before this launch
+    // began.
     __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
         s.nx = dup(-pair_get(a.src, i, 0));
         s.ny = dup(-pair_get(a.src, i, 1));
@@ -325,6 +330,126 @@ __device__ __forceinline__ void chunk_rounds_smem(const float4 *rb, const typena
     }
 }
 
+// Tiled launches: the partials of one tile, [slot][side][k][b] (slot = the
+// block pair's index in its tile, side 0 = the i side for block bi, 1 = the
+// j side for block bj, b = body within the block), and the partner range of
+// a block in a tile. tile_partner returns the first partner block and their
+// count for block `beta` (0 if the tile does not touch it); partner p's
+// partial is at slot tile_slot(g, beta, p) and side p < beta.
+__device__ __forceinline__ int tile_partners(const SymTile &g, int beta, int &p0) {
+    if (beta >= g.c0 && beta < g.c0 + g.hc) {  // column strip (and the diagonal tile's strip)
+        p0 = g.r0;
+        return g.hr;
+    }
+    if (g.I != g.J && beta >= g.r0 && beta < g.r0 + g.hr) {  // row strip
+        p0 = g.c0;
+        return g.hc;
+    }
+    p0 = 0;
+    return 0;
+}
+__device__ __forceinline__ int tile_slot(const SymTile &g, int bi, int bj) {
+    if (g.I == g.J) {
+        const int r = bi - g.r0, c = bj - g.r0;
+        return r * g.hr - r * (r - 1) / 2 + (c - r);
+    }
+    return (bi - g.r0) * g.hc + (bj - g.c0);
+}
+
+// Add tile `t`'s partials of body `o` of block `beta`, all NA sums, to the
+// running sums (hi, lo) in partner order; the tile whose first partner is
+// block 0 starts them. FP32 sums, or two-sums in the precision form, as the
+// one-launch epilogue adds its partials.
+template <class S, int B>
+__device__ __forceinline__ void tile_fold_body(const ForceArgs &a, const float *acc, const float *buf,
+                                               const SymTile &g, int beta, int o, float (&h)[S::NACC],
+                                               float (&l)[S::NACC]) {
+    constexpr int NA = S::NACC;
+    int p0;
+    const int np = tile_partners(g, beta, p0);
+    const int64_t b = (int64_t)beta * B + o;
+    if (p0 == 0) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) h[k] = l[k] = 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            h[k] = __ldcg(acc + (int64_t)k * a.npad + b);
+            l[k] = S::COMP ? __ldcg(acc + (int64_t)(NA + k) * a.npad + b) : 0.f;
+        }
+    }
+    // partners in batches: the batch's loads are in flight together (the
+    // fold is bound by L2 round trips, not bytes), then added in order
+    constexpr int PB = NA <= 4 ? 8 : 4;
+    for (int q0 = 0; q0 < np; q0 += PB) {
+        float v[PB][NA];
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            const int p = p0 + q0 + j;
+            if (q0 + j < np) {
+                const int side = p < beta ? 1 : 0;
+                const int slot = side ? tile_slot(g, p, beta) : tile_slot(g, beta, p);
+                const float *src = buf + ((int64_t)(slot * 2 + side) * NA) * B + o;
+#pragma unroll
+                for (int k = 0; k < NA; ++k) v[j][k] = __ldcs(src + k * B);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            if (q0 + j >= np) break;
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                if constexpr (S::COMP) {
+                    float sum, e;
+                    two_sum(h[k], v[j][k], sum, e);
+                    h[k] = sum;
+                    l[k] = __fadd_rn(l[k], e);
+                } else {
+                    h[k] += v[j][k];
+                }
+            }
+        }
+    }
+}
+
+// Floats of one tile buffer: w x w slots of 2 sides x NA sums x B bodies.
+// `part` holds two of them (tiles alternate), then the running sums
+// [2][NA][npad].
+template <class S, int B>
+__host__ __device__ constexpr int64_t tile_buf_floats(int w) {
+    return (int64_t)w * w * 2 * S::NACC * B;
+}
+
+// Fold the previous tile into the running sums: units of W x 32 bodies of
+// the blocks it touched (its row strip, then its column strip), one body per
+// thread, spread over this launch's CTAs. Not inlined: the pair loop before
+// the call keeps all the registers (inlined, this code cost the loop 2.6 %
+// at N = 262144 without ever running).
+template <class S, int W>
+__device__ __noinline__ void tile_fold_prev(const ForceArgs &a) {
+    constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
+    const int nb = (int)(a.npad / B);
+    float *P = reinterpret_cast<float *>(a.part);
+    const SymTile pg = sym_tile(a.tile - 1, nb, a.tile_w);
+    const float *pbuf = P + ((a.tile - 1) & 1) * tile_buf_floats<S, B>(a.tile_w);
+    float *acc = P + 2 * tile_buf_floats<S, B>(a.tile_w);
+    const int nblk = pg.I == pg.J ? pg.hr : pg.hr + pg.hc;
+    constexpr int kUnits = B / (W * 32);  // units per block
+    for (int u = blockIdx.x; u < nblk * kUnits; u += gridDim.x) {
+        const int kb = u / kUnits;
+        const int beta = kb < pg.hr ? pg.r0 + kb : pg.c0 + (kb - pg.hr);
+        const int o = (u % kUnits) * (W * 32) + threadIdx.x;
+        float h[NA], lo[NA];
+        tile_fold_body<S, B>(a, acc, pbuf, pg, beta, o, h, lo);
+        const int64_t b = (int64_t)beta * B + o;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            __stcg(acc + (int64_t)k * a.npad + b, h[k]);
+            if (S::COMP) __stcg(acc + (int64_t)(NA + k) * a.npad + b, lo[k]);
+        }
+    }
+}
+
 // Resident CTAs per SM that keep a policy's registers at its target (the
 // compiler's own choice without a bound; a bound of 1 CTA let it take 210 for
 // the VJP).
@@ -333,16 +458,38 @@ constexpr int sym_min_blocks() {
     return 65536 / (W * 32 * S::REGS) > 0 ? 65536 / (W * 32 * S::REGS) : 1;
 }
 
-template <class S, int W>
+// TILED: one launch per tile (the launch's tile and its fold of the previous
+// tile); otherwise one launch over every block pair. Two instances, so that
+// the tile code does not change the code of the one-launch kernel.
+template <class S, int W, bool TILED>
 __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(const ForceArgs a) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
     extern __shared__ float acc_j[];  // [W][NA][B]
-    // the previous kernel on the stream (last step's epilogue reads P and
-    // writes the records read here) must be complete
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the previous step's epilogue (it reads the partials and writes the
+    // records read here) must be complete: the first (or only) launch of a
+    // step waits for it; a later tile launch starts early, its records
+    // written before the step's first tile began, and waits below before
+    // it writes partials
+    if (!TILED || a.tile == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
+    // tiles: the next tile's CTAs may take the SMs this launch's last wave
+    // leaves (each waits for this grid before writing anything)
+    if constexpr (TILED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nb = (int)(a.npad / B);
     int bi, bj;
-    sym_item(blockIdx.x, nb, bi, bj);
+    if constexpr (TILED) {
+        const SymTile g = sym_tile(a.tile, nb, a.tile_w);
+        if (g.I == g.J) {
+            int r, cc;
+            tri_item(blockIdx.x, g.hr, r, cc);
+            bi = g.r0 + r;
+            bj = g.r0 + cc;
+        } else {
+            bi = g.r0 + (int)(blockIdx.x / g.hc);
+            bj = g.c0 + (int)(blockIdx.x % g.hc);
+        }
+    } else {
+        sym_item(blockIdx.x, nb, bi, bj);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int next = (l + 1) & 31;
     typename S::C c;
@@ -406,28 +553,57 @@ __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(c
         }
     }
     float *P = reinterpret_cast<float *>(a.part);
-    const int64_t np = a.npad;
-    {
-        float *p = P + (int64_t)bj * NA * np + gbase;
+    if constexpr (TILED) {
+        // the previous tile's grid is complete: its partials are final for
+        // the fold below, and this buffer (the tile before it) is folded;
+        // this item's partials go to its slot of the buffer
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        float *pi = P + (a.tile & 1) * tile_buf_floats<S, B>(a.tile_w) + ((int64_t)blockIdx.x * 2) * NA * B;
+        float *pj = pi + NA * B;
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int k = 0; k < NA; ++k) __stcg(p + k * np + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
-    }
-    if (!diag) {
-        __syncthreads();
-        float *p = P + (int64_t)bi * NA * np + (int64_t)bj * B;
-        for (int t = threadIdx.x; t < B; t += W * 32) {
+            for (int k = 0; k < NA; ++k) __stcg(pi + k * B + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
+        if (!diag) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < B; t += W * 32) {
 #pragma unroll
-            for (int k = 0; k < NA; ++k) {
-                float s = 0.f;
+                for (int k = 0; k < NA; ++k) {
+                    float s = 0.f;
 #pragma unroll
-                for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
-                __stcg(p + k * np + t, s);
+                    for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
+                    __stcg(pj + k * B + t, s);
+                }
+            }
+        }
+    } else {
+        const int64_t np = a.npad;
+        {
+            float *p = P + (int64_t)bj * NA * np + gbase;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < NA; ++k) __stcg(p + k * np + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
+        }
+        if (!diag) {
+            __syncthreads();
+            float *p = P + (int64_t)bi * NA * np + (int64_t)bj * B;
+            for (int t = threadIdx.x; t < B; t += W * 32) {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
+                    __stcg(p + k * np + t, s);
+                }
             }
         }
     }
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if constexpr (!TILED) {
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        return;
+    }
+    if (a.tile > 0) tile_fold_prev<S, W>(a);
 }
 
 // Sum of the nb partials of each body in block order (the policy's Fin:
@@ -477,6 +653,38 @@ __global__ void __launch_bounds__(32 * S::NACC) sym_finish_kernel(const ForceArg
     // 182 against 100 us per step at N = 16384 (measured).
 }
 
+// After the last tile: its partials folded into the running sums of the
+// bodies it touches, then the policy's epilogue for every body (one thread
+// per body; the sums of every other body are complete in `acc`).
+template <class S, int B>
+__global__ void __launch_bounds__(128) sym_tile_final_kernel(const ForceArgs a) {
+    constexpr int NA = S::NACC;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int nb = (int)(a.npad / B);
+    const SymTile g = sym_tile(a.ntile - 1, nb, a.tile_w);
+    const int beta = (int)(i / B), o = (int)(i % B);
+    const float *P = reinterpret_cast<const float *>(a.part);
+    const float *acc = P + 2 * tile_buf_floats<S, B>(a.tile_w);
+    float h[NA], l[NA];
+    int p0;
+    if (tile_partners(g, beta, p0) > 0) {
+        tile_fold_body<S, B>(a, acc, P + ((a.ntile - 1) & 1) * tile_buf_floats<S, B>(a.tile_w), g, beta, o,
+                             h, l);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            h[k] = __ldcg(acc + (int64_t)k * a.npad + i);
+            l[k] = S::COMP ? __ldcg(acc + (int64_t)(NA + k) * a.npad + i) : 0.f;
+        }
+    }
+    typename S::Fin f;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) S::fin_set(f, k, h[k], l[k]);
+    S::finish(a, i, f);
+}
+
 cudaError_t launch_ex(const void *fn, dim3 grid, dim3 block, size_t smem, bool pdl,
                       const ForceArgs &a, cudaStream_t st) {
     cudaLaunchConfig_t cfg;
@@ -504,13 +712,32 @@ template <class S, int W>
 cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
     constexpr int B = W * 32 * S::R;
     constexpr size_t smem = sym_smem<S, W>();
-    auto k = sym_kernel<S, W>;
+    auto k = sym_kernel<S, W, false>;
+    auto kt = sym_kernel<S, W, true>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int64_t nb = a.npad / B;
     if (nb * B != a.npad || nb != a.ntiles) return cudaErrorInvalidValue;
+    if (a.tile_w > 0) {
+        // one launch per tile, each a programmatic dependent of the one
+        // before; then the last fold and the epilogue
+        const int nt = sym_tile_count((int)nb, a.tile_w);
+        if (nt != a.ntile) return cudaErrorInvalidValue;
+        ForceArgs t = a;
+        for (int s = 0; s < nt; ++s) {
+            t.tile = s;
+            const SymTile g = sym_tile(s, (int)nb, a.tile_w);
+            cudaError_t e = launch_ex((const void *)kt, dim3((unsigned)g.items()), dim3(W * 32), smem,
+                                      s == 0 ? a.pdl != 0 : true, t, st);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_ex((const void *)sym_tile_final_kernel<S, B>, dim3((unsigned)((a.n + 127) / 128)),
+                         dim3(128), 0, true, t, st);
+    }
     const unsigned items = (unsigned)(nb * (nb + 1) / 2);
     cudaError_t e = launch_ex((const void *)k, dim3(items), dim3(W * 32), smem, a.pdl != 0, a, st);
     if (e != cudaSuccess) return e;
@@ -523,7 +750,7 @@ cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
 template <class S, int W>
 int occ_sym(int) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel<S, W>, W * 32, sym_smem<S, W>()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel<S, W, false>, W * 32, sym_smem<S, W>()) !=
         cudaSuccess)
         return 0;
     return b;

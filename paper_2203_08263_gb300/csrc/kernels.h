@@ -39,8 +39,59 @@ constexpr int kSymVjpR = NB_SYM_VJP_R;
 inline bool pol_is_sym(int pol) { return pol == kPolSym || pol == kPolVjpSym || pol == kPolSymComp; }
 // sums per body of a pair-symmetric policy (its partials: nb x sums x npad floats)
 inline int sym_sums(int pol) { return pol == kPolVjpSym ? 8 : 3; }
-// Above this many bytes of partials the one-sided policy serves.
+// Above this many bytes of partials the ensemble's pair-symmetric form
+// falls back to the one-sided items.
 constexpr size_t kSymMaxPartBytes = (size_t)16 << 30;
+
+// Pair t of the upper triangle of an n x n grid, row-major: rows r = 0..n-1
+// holding columns c = r..n-1.
+__host__ __device__ inline void tri_item(int64_t t, int n, int &r, int &c) {
+    const double k = 2.0 * n + 1.0;
+    int64_t q = (int64_t)((k - sqrt(k * k - 8.0 * (double)t)) * 0.5);
+    if (q < 0) q = 0;
+    if (q > n - 1) q = n - 1;
+    auto start = [n](int64_t row) { return row * n - row * (row - 1) / 2; };
+    while (q > 0 && start(q) > t) --q;
+    while (q < n - 1 && start(q + 1) <= t) ++q;
+    r = (int)q;
+    c = (int)(q + (t - start(q)));
+}
+
+// Tiles of the pair-symmetric kernels' triangle of block pairs: the nb blocks
+// are cut into strips of w; tile (I, J), I <= J, holds the block pairs
+// (bi, bj), bi <= bj, with bi in strip I and bj in strip J. Tiles are numbered
+// row-major over the triangle of strips: every body then meets its partner
+// blocks p in ascending order across tiles (p < its block through the tiles
+// of its column strip, top down, the rest through the tiles of its row
+// strip, left to right), so a running sum over tiles adds the partials in
+// the same order as one sum over all of them.
+struct SymTile {
+    int I, J;    // strips
+    int r0, c0;  // first block of strip I, of strip J
+    int hr, hc;  // blocks in strip I, in strip J
+    __host__ __device__ int items() const { return I == J ? hr * (hr + 1) / 2 : hr * hc; }
+};
+__host__ __device__ inline int sym_tile_count(int nb, int w) {
+    const int m = (nb + w - 1) / w;
+    return m * (m + 1) / 2;
+}
+__host__ __device__ inline SymTile sym_tile(int t, int nb, int w) {
+    SymTile g;
+    tri_item(t, (nb + w - 1) / w, g.I, g.J);
+    g.r0 = g.I * w;
+    g.c0 = g.J * w;
+    g.hr = nb - g.r0 < w ? nb - g.r0 : w;
+    g.hc = nb - g.c0 < w ? nb - g.c0 : w;
+    return g;
+}
+// Tiles of the pair-symmetric forms are used above this many bytes of
+// partials for one launch over all block pairs; two tile buffers take at
+// most kSymTileBufBytes. Measured at N = 262144 (805 MB of partials in one
+// launch): 3.99e12 interactions/s in one launch, 3.94e12 by tiles of 24 to
+// 96 blocks; below the threshold the partials' footprint is not worth that
+// 1 %.
+constexpr size_t kSymTileAbove = (size_t)2 << 30;
+constexpr size_t kSymTileBufBytes = (size_t)64 << 20;
 
 struct Shape {
     int pol, nt, r, split, jt;

@@ -11,7 +11,8 @@ Input: Plummer sphere (seed 1), eps = 0.05. Prints the CUDA-event time per
 call and the rate at 20 flops per interaction (--pol adjoint: one nb_adjoint
 over a trajectory of --steps steps checkpointed every --ckpt-every, after
 that trajectory is run). --form / --vjp-form pin the force form (one-sided or
-a pair-symmetric block size). --peaks runs the FFMA, f32x2-FMA and MUFU
+a pair-symmetric block size); --tile sets the pair-symmetric launches (one
+launch, or tiles of w x w block pairs). --peaks runs the FFMA, f32x2-FMA and MUFU
 micro-benchmarks instead.
 """
 from __future__ import annotations
@@ -38,6 +39,8 @@ def main():
                     help="FP32 force form: 0 chosen per size, 1 one-sided, 512/1024 pair-symmetric blocks")
     ap.add_argument("--vjp-form", type=int, default=0,
                     help="FP32 VJP form: 0 chosen per size, 1 one-sided, 256/512 pair-symmetric blocks")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="pair-symmetric launches: 0 chosen per size, -1 one launch, w tiles of w blocks")
     ap.add_argument("--peaks", action="store_true")
     a = ap.parse_args()
 
@@ -45,7 +48,7 @@ def main():
 
     from paper_2203_08263_gb300 import build, ics
     from paper_2203_08263_gb300.nbody import (MODE_ADJOINT, MODE_FORWARD, MODE_POTENTIAL, NB_DBG_FORM,
-                                              NB_DBG_RUN_PATH, NB_DBG_VJP_FORM, Context)
+                                              NB_DBG_RUN_PATH, NB_DBG_SYM_TILE, NB_DBG_VJP_FORM, Context)
 
     build.build()
     if a.peaks:
@@ -62,6 +65,7 @@ def main():
     ctx.debug_set(NB_DBG_RUN_PATH, a.path)
     ctx.debug_set(NB_DBG_FORM, a.form)
     ctx.debug_set(NB_DBG_VJP_FORM, a.vjp_form)
+    ctx.debug_set(NB_DBG_SYM_TILE, a.tile)
     x, v, m = (torch.tensor(t, dtype=f, device=dev) for t in (s.x, s.v, s.m))
     ab = torch.tensor(np.random.default_rng(0).normal(size=(a.n, 3)), dtype=f, device=dev)
     mode = {"fp32": MODE_FORWARD, "comp": MODE_FORWARD, "vjp": MODE_ADJOINT, "vjp-comp": MODE_ADJOINT,

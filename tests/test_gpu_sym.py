@@ -308,3 +308,76 @@ def test_sym_compensated_close_encounters(nbm, block, n):
     err = rel_l2(a[idx], oracle.accel(s.x, s.m, G, eps, idx))
     print(f"precision form, cube eps=0.01, n={n}, block {block}: rel L2 {err:.3e}")
     assert err <= 1e-6
+
+
+# ------------------------------------------------------------ tiled launches
+
+@pytest.mark.parametrize("w", [1, 3, 7])
+def test_sym_tiled_launches_bit_identical(nbm, w):
+    """The pair-symmetric kernels launched tile by tile (w x w block pairs per
+    launch, the partials of each tile folded into running sums in partner
+    order) give bit for bit the results of one launch over all block pairs:
+    forces, a run, the precision form and the VJP, with ragged last strips
+    (20 blocks of 1024 bodies; 35 of 512 for the VJP)."""
+    n = 20000
+    s = ics.plummer(n, seed=31)
+    G, eps = 1.0, 0.05
+    ab = np.random.default_rng(5).normal(size=(n, 3))
+    out = {}
+    for tile in (-1, w):
+        ctx = nbm.Context(G, eps, 1e-3)
+        ctx.debug_set(nbm.NB_DBG_FORM, 1024)
+        ctx.debug_set(nbm.NB_DBG_VJP_FORM, 512)
+        ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+        ctx.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+        before = ctx.launch_count
+        a = ctx.accel(_t(s.x), _t(s.m))
+        ctx.sync()
+        m_ = (20 + w - 1) // w
+        # the pack, then one launch per tile and the final sum (or the pair kernel and its sum)
+        assert ctx.launch_count - before == 1 + (m_ * (m_ + 1) // 2 + 1 if tile > 0 else 2)
+        x, v, m = _t(s.x), _t(s.v), _t(s.m)
+        ctx.run(x, v, m, 6)  # each position buffer read three times
+        xb, mb = ctx.vjp(_t(s.x), _t(s.m), _t(ab))
+        comp = nbm.Context(G, eps, 1e-3, precision="comp")
+        comp.debug_set(nbm.NB_DBG_FORM, 1024)
+        comp.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+        ac = comp.accel(_t(s.x, torch.float64), _t(s.m, torch.float64))
+        ctx.sync()
+        comp.sync()
+        out[tile] = [t.clone() for t in (a, x, v, xb, mb, ac)]
+    for got, ref in zip(out[w], out[-1]):
+        assert torch.equal(got, ref)
+    assert rel_l2(to_np(out[w][0]), oracle.accel(s.x, s.m, G, eps)) <= 2e-5
+    assert rel_l2(to_np(out[w][5]), oracle.accel(s.x, s.m, G, eps)) <= 1e-6
+
+
+def test_sym_tiles_by_default_at_large_n(nbm):
+    """Above 2 GiB of partials for one launch the forces go by tiles: at
+    N = 524288 (1024-body blocks, 3.2 GB of partials in one launch) a step is
+    the pack, one launch per tile and the final sum."""
+    n = 524288
+    ctx = nbm.Context(1.0, 0.05, 1e-3)
+    if ctx.get_config(n)["tuned"]:
+        pytest.skip("a tuning table is loaded")
+    s = ics.plummer(n, seed=1)
+    x, v, m = _t(s.x), _t(s.v), _t(s.m)
+    before = ctx.launch_count
+    ctx.run(x, v, m, 1)
+    ctx.sync()
+    assert ctx.launch_count - before > 3
+
+
+def test_sym_two_million_bodies_sampled(nbm):
+    """N = 2^21 Plummer in FP32: the pair-symmetric form (by tiles; one launch
+    would need 51.5 GB of partials), 1024 sampled bodies against the FP64
+    oracle at the plain FP32 bound."""
+    n, G, eps = 1 << 21, 1.0, 0.05
+    s = ics.plummer(n, seed=7)
+    ctx = nbm.Context(G, eps, 1e-3)
+    assert ctx.get_config(n)["form"] == "pair_symmetric"
+    a = to_np(ctx.accel(_t(s.x), _t(s.m)))
+    idx = ics.subset_indices(n, 1024, 8)
+    err = rel_l2(a[idx], oracle.accel(s.x, s.m, G, eps, idx))
+    print(f"N = 2^21 pair-symmetric (tiled) accel, 1024 sampled bodies: rel L2 {err:.3e}")
+    assert err <= 2e-5
