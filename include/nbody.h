@@ -283,7 +283,8 @@ typedef enum {
     NB_FORM_POW = 7,             /* ablation: powf */
     NB_FORM_PAIR_SYMMETRIC = 8,  /* FP32, each unordered pair once */
     NB_FORM_VJP_PAIR_SYMMETRIC = 9, /* adjoint VJP, FP32, each unordered pair once */
-    NB_FORM_COMPENSATED_PAIR_SYMMETRIC = 10 /* compensated, FP64 state, each pair once */
+    NB_FORM_COMPENSATED_PAIR_SYMMETRIC = 10, /* compensated, FP64 state, each pair once */
+    NB_FORM_VJP_COMPENSATED_PAIR_SYMMETRIC = 11 /* adjoint VJP, compensated, FP64 state, each pair once */
 } nb_form;
 
 /* The force-sum form (nb_form) the context would use for (n, mode), mode as
@@ -334,9 +335,9 @@ typedef enum {
      * (nb_run's graph path; the fused small-system paths keep their own
      * kernel). */
     NB_DBG_FORM = 5,
-    /* FP32 VJP form (nb_vjp, nb_adjoint): 0 = chosen per size (default),
-     * 1 = one-sided only, 256 or 512 = the pair-symmetric kernel with blocks
-     * of that many bodies at every size. */
+    /* VJP form (nb_vjp, nb_adjoint; FP32 and the precision form): 0 =
+     * chosen per size (default), 1 = one-sided only, 256 or 512 = the
+     * pair-symmetric kernel with blocks of that many bodies at every size. */
     NB_DBG_VJP_FORM = 6,
     /* Pair-symmetric launches (forces, precision form, VJP): 0 = chosen per
      * size (default: one launch over all block pairs up to 2 GiB of

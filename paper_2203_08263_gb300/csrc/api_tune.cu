@@ -25,7 +25,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode) {
         else if (ctx->math == 0 && n >= 8192) pols = {kPolF32x2, kPolScalar, kPolSym};
         else pols = {kPolF32x2, kPolScalar};
     } else if (f64_state(ctx)) {
-        pols = {kPolVjpComp};
+        pols = n >= 2048 ? std::vector<int>{kPolVjpComp, kPolVjpSymComp} : std::vector<int>{kPolVjpComp};
     } else {
         pols = n >= 2048 ? std::vector<int>{kPolVjp, kPolVjpSym} : std::vector<int>{kPolVjp};
     }

@@ -21,6 +21,7 @@ const ForceEntry *table_pow(int *count);
 const ForceEntry *table_sym(int *count);
 const ForceEntry *table_vjp_sym(int *count);
 const ForceEntry *table_comp_sym(int *count);
+const ForceEntry *table_vjp_comp_sym(int *count);
 
 const ForceEntry *force_table(int pol, int *count) {
     switch (pol) {
@@ -35,11 +36,13 @@ const ForceEntry *force_table(int pol, int *count) {
         case kPolSym: return table_sym(count);
         case kPolVjpSym: return table_vjp_sym(count);
         case kPolSymComp: return table_comp_sym(count);
+        case kPolVjpSymComp: return table_vjp_comp_sym(count);
         default: *count = 0; return nullptr;
     }
 }
 int pol_rec_f4(int pol) {
-    return (pol == kPolVjp || pol == kPolVjpSym) ? 4 : (pol == kPolVjpComp ? 5 : 2);
+    if (pol == kPolVjp || pol == kPolVjpSym) return 4;
+    return (pol == kPolVjpComp || pol == kPolVjpSymComp) ? 5 : 2;
 }
 int pol_part_f4(int pol) {
     switch (pol) {
@@ -211,11 +214,11 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     } else if (pol == kPolPot) {
         r = 2;
         if (n >= 4096) jt = 128;
-    } else if (pol == kPolVjp && allow_sym && n >= 8192) {
+    } else if ((pol == kPolVjp || pol == kPolVjpComp) && allow_sym && n >= 8192) {
         // each unordered pair once: blocks of 256 bodies below 2^16, 512 from there
         const int snt = n >= 65536 ? 128 : 64;
         const int64_t b = (int64_t)snt * kSymVjpR;
-        return Shape{kPolVjpSym, snt, kSymVjpR, 1, (int)b};
+        return Shape{pol == kPolVjp ? kPolVjpSym : kPolVjpSymComp, snt, kSymVjpR, 1, (int)b};
     } else {  // VJP (the precision form's R = 2 instance spills at the 128-register cap)
         r = (n >= 8192 && pol == kPolVjp) ? 2 : 1;
         if (n >= 4096) jt = 128;
@@ -244,8 +247,9 @@ nb_status choose_shape(nb_ctx *ctx, int mode, int64_t n, Shape *out, bool *from_
                      ctx->form_pin};
         return NB_OK;
     }
-    if (pol == kPolVjp && ctx->vjp_form_pin > 1) {
-        *out = Shape{kPolVjpSym, ctx->vjp_form_pin / kSymVjpR, kSymVjpR, 1, ctx->vjp_form_pin};
+    if ((pol == kPolVjp || pol == kPolVjpComp) && ctx->vjp_form_pin > 1) {
+        *out = Shape{pol == kPolVjp ? kPolVjpSym : kPolVjpSymComp, ctx->vjp_form_pin / kSymVjpR, kSymVjpR, 1,
+                     ctx->vjp_form_pin};
         return NB_OK;
     }
     const int pin = mode == 1 ? ctx->vjp_form_pin : ctx->form_pin;

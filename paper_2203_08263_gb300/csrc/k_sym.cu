@@ -211,9 +211,14 @@ struct SymVjp {
     template <bool MASK>
     __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
                                                 float2 (&aj)[NACC], const C &c, float2 keep) {
-        const float2 dx = __fadd2_rn(j.x, s.nx);
-        const float2 dy = __fadd2_rn(j.y, s.ny);
-        const float2 dz = __fadd2_rn(j.z, s.nz);
+        terms<MASK>(__fadd2_rn(j.x, s.nx), __fadd2_rn(j.y, s.ny), __fadd2_rn(j.z, s.nz), j, s, ai, aj,
+                    c, keep);
+    }
+    // The pair's terms for both bodies from the separation d = x_j - x_i.
+    template <bool MASK>
+    __device__ __forceinline__ static void terms(float2 dx, float2 dy, float2 dz, const J &j, const I &s,
+                                                 float2 (&ai)[NACC], float2 (&aj)[NACC], const C &c,
+                                                 float2 keep) {
         float2 q = __ffma2_rn(dx, dx, c.eps2);
         q = __ffma2_rn(dy, dy, q);
         q = __ffma2_rn(dz, dz, q);
@@ -255,6 +260,101 @@ struct SymVjp {
         f.ux = s[0]; f.uy = s[1]; f.uz = s[2]; f.v = s[3];
         f.wx = s[4]; f.wy = s[5]; f.wz = s[6]; f.p = s[7];
         VjpF32x2::finish(a, k, f);
+    }
+};
+
+// Precision form of the VJP (FP64 state): the records of the one-sided
+// VjpComp policy, {x0,x1,y0,y1} {z0,z1,m0,m1} {ax0,ax1,ay0,ay1}
+// {az0,az1,xl0,xl1} {yl0,yl1,zl0,zl1} (the FP32 low parts of the FP64
+// positions), d formed as (x_j^hi - x_i^hi) + (x_j^lo - x_i^lo) so that it
+// keeps FP32 relative accuracy for close pairs (whose terms weigh as
+// |d|^-3 ... |d|^-5), the pair terms of SymVjp, FP32 sums within a block
+// pair, and the block-pair partials two-summed in the epilogue, which widens
+// them and updates x-bar and m-bar in FP64 as the one-sided policy does.
+#ifndef NB_SYM_VJP_COMP_REGS
+#define NB_SYM_VJP_COMP_REGS 168
+#endif
+struct SymVjpComp {
+    static constexpr int R = kSymVjpR;
+    static constexpr bool REC_SMEM = NB_SYM_VJP_REC_SMEM;
+    static constexpr int REGS = NB_SYM_VJP_COMP_REGS;
+    static constexpr int NACC = 8;
+    static constexpr int REC_F4 = 5;
+    static constexpr bool SELF_MASK = true;
+    __host__ __device__ static constexpr float jsign(int k) { return SymVjp::jsign(k); }
+    struct I {
+        SymVjp::I b;
+        float2 nlx, nly, nlz;
+    };
+    struct J {
+        SymVjp::J b;
+        float2 xl, yl, zl;
+    };
+    using C = SymVjp::C;
+    __device__ static void consts(const ForceArgs &a, C &c) { SymVjp::consts(a, c); }
+    __device__ static float get(const float4 *base, int64_t i, int c) {
+        const float *p = reinterpret_cast<const float *>(base + (i >> 1) * 5);
+        return p[2 * c + (int)(i & 1)];
+    }
+    __device__ static void load_i(const ForceArgs &a, int64_t i, I &s) {
+        s.b.nx = dup(-get(a.src, i, 0));
+        s.b.ny = dup(-get(a.src, i, 1));
+        s.b.nz = dup(-get(a.src, i, 2));
+        s.b.nm = dup(-get(a.src, i, 3));
+        s.b.ax = dup(get(a.src, i, 4));
+        s.b.ay = dup(get(a.src, i, 5));
+        s.b.az = dup(get(a.src, i, 6));
+        s.nlx = dup(-get(a.src, i, 7));
+        s.nly = dup(-get(a.src, i, 8));
+        s.nlz = dup(-get(a.src, i, 9));
+    }
+    __device__ static void from_f4(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                   const float4 &r4, J &j) {
+        j.b.x = f2(r0.x, r0.y);
+        j.b.y = f2(r0.z, r0.w);
+        j.b.z = f2(r1.x, r1.y);
+        j.b.m = f2(r1.z, r1.w);
+        j.b.ax = f2(r2.x, r2.y);
+        j.b.ay = f2(r2.z, r2.w);
+        j.b.az = f2(r3.x, r3.y);
+        j.xl = f2(r3.z, r3.w);
+        j.yl = f2(r4.x, r4.y);
+        j.zl = f2(r4.z, r4.w);
+    }
+    __device__ static void load_j(const float4 *rec, J &j) {
+        from_f4(__ldg(rec), __ldg(rec + 1), __ldg(rec + 2), __ldg(rec + 3), __ldg(rec + 4), j);
+    }
+    __device__ static void shfl(J &j, int src) {
+        SymVjp::shfl(j.b, src);
+        j.xl = shfl2(j.xl, src);
+        j.yl = shfl2(j.yl, src);
+        j.zl = shfl2(j.zl, src);
+    }
+    __device__ static void load_j_smem(const float4 *rb, int q, J &j) {
+        from_f4(rb[q], rb[32 + q], rb[64 + q], rb[96 + q], rb[128 + q], j);
+    }
+    template <bool MASK>
+    __device__ __forceinline__ static void pair(const J &j, const I &s, float2 (&ai)[NACC],
+                                                float2 (&aj)[NACC], const C &c, float2 keep) {
+        const float2 dx = __fadd2_rn(__fadd2_rn(j.b.x, s.b.nx), __fadd2_rn(j.xl, s.nlx));
+        const float2 dy = __fadd2_rn(__fadd2_rn(j.b.y, s.b.ny), __fadd2_rn(j.yl, s.nly));
+        const float2 dz = __fadd2_rn(__fadd2_rn(j.b.z, s.b.nz), __fadd2_rn(j.zl, s.nlz));
+        SymVjp::terms<MASK>(dx, dy, dz, j.b, s.b, ai, aj, c, keep);
+    }
+    static constexpr bool COMP = true;
+    struct Fin { float h[NACC], l[NACC]; };
+    __device__ static void fin_set(Fin &f, int k, float h, float l) {
+        f.h[k] = h;
+        f.l[k] = l;
+    }
+    __device__ static void finish(const ForceArgs &a, int64_t k, const Fin &fin) {
+        VjpComp::F f;
+#pragma unroll
+        for (int q = 0; q < NACC; ++q) {
+            f.h[q] = fin.h[q];
+            f.l[q] = fin.l[q];
+        }
+        VjpComp::finish(a, k, f);
     }
 };
 
@@ -767,6 +867,10 @@ const ForceEntry kComp[] = {
     {64, SymComp::R, &launch_sym<SymComp, 2>, &occ_sym<SymComp, 2>},   // blocks of 512
     {128, SymComp::R, &launch_sym<SymComp, 4>, &occ_sym<SymComp, 4>},  // blocks of 1024
 };
+const ForceEntry kVjpComp[] = {
+    {64, SymVjpComp::R, &launch_sym<SymVjpComp, 2>, &occ_sym<SymVjpComp, 2>},   // blocks of 256
+    {128, SymVjpComp::R, &launch_sym<SymVjpComp, 4>, &occ_sym<SymVjpComp, 4>},  // blocks of 512
+};
 const ForceEntry kVjp[] = {
     {64, SymVjp::R, &launch_sym<SymVjp, 2>, &occ_sym<SymVjp, 2>},   // blocks of 256
     {128, SymVjp::R, &launch_sym<SymVjp, 4>, &occ_sym<SymVjp, 4>},  // blocks of 512
@@ -782,6 +886,11 @@ const ForceEntry *table_sym(int *count) {
 const ForceEntry *table_comp_sym(int *count) {
     *count = (int)(sizeof(kComp) / sizeof(kComp[0]));
     return kComp;
+}
+
+const ForceEntry *table_vjp_comp_sym(int *count) {
+    *count = (int)(sizeof(kVjpComp) / sizeof(kVjpComp[0]));
+    return kVjpComp;
 }
 
 const ForceEntry *table_vjp_sym(int *count) {

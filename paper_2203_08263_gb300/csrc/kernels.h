@@ -21,13 +21,14 @@ enum Pol : int {
     kPolSym = 8,     // plain FP32 forces, each unordered pair once (csrc/k_sym.cu)
     kPolVjpSym = 9,  // adjoint VJP, FP32 state, each unordered pair once (csrc/k_sym.cu)
     kPolSymComp = 10,  // compensated forces, FP64 state, each unordered pair once (csrc/k_sym.cu)
-    kPolCount = 11
+    kPolVjpSymComp = 11,  // adjoint VJP, compensated, FP64 state, each unordered pair once (csrc/k_sym.cu)
+    kPolCount = 12
 };
 
 // Bodies per lane of the pair-symmetric force policy; its table holds blocks
 // of 32 x R x (1, 2 or 4 warps) = 256, 512 or 1024 bodies (Shape: nt = 32,
-// 64 or 128, r = R, jt = the block, split = 1). The VJP's holds R = 4,
-// blocks of 256 or 512 bodies.
+// 64 or 128, r = R, jt = the block, split = 1). The VJP's (FP32 and the
+// precision form) hold R = 4, blocks of 256 or 512 bodies.
 #ifndef NB_SYM_R
 #define NB_SYM_R 8  // measured at N = 262144: 3.70e12 interactions/s at R = 6 (96 registers, 5 CTAs per SM), 3.98e12 at 8, 3.99e12 at 10
 #endif
@@ -36,9 +37,11 @@ constexpr int kSymR = NB_SYM_R;
 #define NB_SYM_VJP_R 4
 #endif
 constexpr int kSymVjpR = NB_SYM_VJP_R;
-inline bool pol_is_sym(int pol) { return pol == kPolSym || pol == kPolVjpSym || pol == kPolSymComp; }
+inline bool pol_is_sym(int pol) {
+    return pol == kPolSym || pol == kPolVjpSym || pol == kPolSymComp || pol == kPolVjpSymComp;
+}
 // sums per body of a pair-symmetric policy (its partials: nb x sums x npad floats)
-inline int sym_sums(int pol) { return pol == kPolVjpSym ? 8 : 3; }
+inline int sym_sums(int pol) { return pol == kPolVjpSym || pol == kPolVjpSymComp ? 8 : 3; }
 // Above this many bytes of partials the ensemble's pair-symmetric form
 // falls back to the one-sided items.
 constexpr size_t kSymMaxPartBytes = (size_t)16 << 30;

@@ -26,7 +26,7 @@ MODE_FORWARD, MODE_ADJOINT, MODE_POTENTIAL = 0, 1, 2
 # nb_form values (nb_get_form)
 FORMS = {0: "f32x2", 1: "scalar", 2: "compensated", 3: "potential", 4: "vjp",
          5: "vjp_compensated", 6: "sqrt_div", 7: "pow", 8: "pair_symmetric", 9: "vjp_pair_symmetric",
-         10: "compensated_pair_symmetric"}
+         10: "compensated_pair_symmetric", 11: "vjp_compensated_pair_symmetric"}
 
 # Every symbol include/nbody.h declares, with (restype, argtypes).
 _c = ctypes

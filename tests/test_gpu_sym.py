@@ -112,7 +112,8 @@ def test_sym_is_deterministic(nbm):
 
 def test_default_form_by_size(nbm):
     """Untuned forward, both precisions: one-sided below 16384 bodies,
-    pair-symmetric from there, one-sided when pinned; the VJP from 8192."""
+    pair-symmetric from there, one-sided when pinned; the VJP (both
+    precisions) from 8192."""
     ctx = nbm.Context(1.0, 0.01, 1e-3)
     if ctx.get_config(40000)["tuned"]:
         pytest.skip("a tuning table is loaded")
@@ -127,6 +128,9 @@ def test_default_form_by_size(nbm):
     assert comp.get_config(20000)["form"] == "compensated_pair_symmetric"
     comp.debug_set(nbm.NB_DBG_FORM, 1)
     assert comp.get_config(40000)["form"] == "compensated"
+    assert comp.get_config(4000, nbm.MODE_ADJOINT)["form"] == "vjp_compensated"
+    assert comp.get_config(40000, nbm.MODE_ADJOINT)["form"] == "vjp_compensated_pair_symmetric"
+    comp.debug_set(nbm.NB_DBG_VJP_FORM, 1)
     assert comp.get_config(40000, nbm.MODE_ADJOINT)["form"] == "vjp_compensated"
 
 
@@ -381,3 +385,52 @@ def test_sym_two_million_bodies_sampled(nbm):
     err = rel_l2(a[idx], oracle.accel(s.x, s.m, G, eps, idx))
     print(f"N = 2^21 pair-symmetric (tiled) accel, 1024 sampled bodies: rel L2 {err:.3e}")
     assert err <= 2e-5
+
+
+# ------------------------------------------- precision-form VJP, pair-symmetric
+
+@pytest.mark.parametrize("block", [256, 512])
+@pytest.mark.parametrize("n", [2, 65, 513, 2000, 9000])
+def test_sym_vjp_compensated_matches_oracle(nbm, block, n):
+    """The precision form's pair-symmetric VJP (FP64 state; d from the FP32
+    (hi, lo) parts of the positions, FP32 sums within a block pair, the
+    partials two-summed) against the FP64 oracle at the precision form's
+    1e-6 bound, on a cube with eps = 0.01 (close pairs weigh as |d|^-5)."""
+    G, eps = 1.0, 0.01
+    s = ics.cube(n, seed=90 + n)
+    ab = np.random.default_rng(n + 1).normal(size=(n, 3))
+    ctx = nbm.Context(G, eps, 1e-3, precision="comp")
+    ctx.debug_set(nbm.NB_DBG_VJP_FORM, block)
+    assert ctx.get_config(n, nbm.MODE_ADJOINT)["form"] == "vjp_compensated_pair_symmetric"
+    f = torch.float64
+    xb, mb = ctx.vjp(_t(s.x, f), _t(s.m, f), _t(ab, f))
+    rx, rm = oracle.vjp(s.x, s.m, G, eps, ab)
+    ex, em = rel_l2(to_np(xb), rx), rel_l2(to_np(mb), rm)
+    print(f"precision-form pair-symmetric VJP n={n} block {block}: xbar {ex:.2e}, mbar {em:.2e}")
+    assert ex <= 1e-6 and em <= 1e-6
+
+
+@pytest.mark.parametrize("vjp_block", [256, 512])
+def test_sym_adjoint_precision_form_vs_fp64_oracle(nbm, vjp_block):
+    """The precision-form adjoint (N = 64, T = 20, checkpoint every 5) with
+    the pair-symmetric forward recompute and VJP against the FP64 oracle's
+    gradient: within 1e-6 per block."""
+    n, T, k = 64, 20, 5
+    s = ics.cube(n, seed=4, masses="equal")
+    xstar = ics.targets(n, seed=4)
+    G, eps, dt = 1.0, 0.01, 1e-3
+    f = torch.float64
+    ctx = nbm.Context(G, eps, dt, precision="comp")
+    ctx.debug_set(nbm.NB_DBG_FORM, 512)
+    ctx.debug_set(nbm.NB_DBG_VJP_FORM, vjp_block)
+    ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+    x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+    ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+    ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+    xbT = 2 * (x - _t(xstar, f))
+    got = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+    xT, _ = oracle.run(s.x, s.v, s.m, G, eps, dt, T)
+    ref = oracle.adjoint(s.x, s.v, s.m, G, eps, dt, T, 2 * (xT - xstar), np.zeros((n, 3)))
+    errs = [rel_l2(to_np(g), r) for g, r in zip(got, ref)]
+    print("precision-form adjoint, pair-symmetric kernels: %s" % ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-6, errs
