@@ -554,9 +554,22 @@ __device__ __noinline__ void tile_fold_prev(const ForceArgs &a) {
 // compiler's own choice without a bound; a bound of 1 CTA let it take 210 for
 // the VJP).
 template <class S, int W>
-constexpr int sym_min_blocks() {
+__host__ __device__ constexpr int sym_min_blocks() {
     return 65536 / (W * 32 * S::REGS) > 0 ? 65536 / (W * 32 * S::REGS) : 1;
 }
+
+// Record buffers per warp of the staged-record kernels: two unless the
+// second would lower the resident CTAs per SM below what the registers allow
+// (228 KiB of shared memory per SM; the VJP's 512-body blocks: 3 CTAs of 81
+// KiB do not fit, of 73 KiB they do).
+template <class S, int W>
+__host__ __device__ constexpr int rec_bufs() {
+    constexpr size_t base = (size_t)W * S::NACC * (W * 32 * S::R) * 4;
+    constexpr size_t buf = (size_t)W * S::REC_F4 * 32 * 16;
+    // (1 KiB of each CTA's shared memory is reserved by the system)
+    return (base + 2 * buf + 1024) * sym_min_blocks<S, W>() <= (size_t)228 * 1024 ? 2 : 1;
+}
+
 
 // TILED: one launch per tile (the launch's tile and its fold of the previous
 // tile); otherwise one launch over every block pair. Two instances, so that
@@ -606,34 +619,42 @@ __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(c
     }
     const bool diag = bi == bj;
     float *mine = acc_j + w * NA * B;
-    // S::REC_SMEM: this warp's two record buffers, [2][REC_F4][32] float4
-    // after acc_j; chunk ch + 1 is copied while chunk ch is evaluated
-    float4 *rbw = reinterpret_cast<float4 *>(acc_j + W * NA * B) + w * 2 * S::REC_F4 * 32;
+    // S::REC_SMEM: this warp's record buffers after acc_j, [NBUF][REC_F4][32]
+    // float4. With two, chunk ch + 1 is copied while chunk ch is evaluated;
+    // with one (where two would cost a resident CTA per SM), each chunk's copy
+    // is waited for at its start.
+    constexpr int NBUF = rec_bufs<S, W>();
+    float4 *rbw = reinterpret_cast<float4 *>(acc_j + W * NA * B) + w * NBUF * S::REC_F4 * 32;
     auto issue = [&](int ch) {
         const float4 *src = a.src + ((int64_t)bj * (B / 2) + ch * 32 + l) * S::REC_F4;
-        float4 *dst = rbw + (ch & 1) * S::REC_F4 * 32 + l;
+        float4 *dst = rbw + (ch % NBUF) * S::REC_F4 * 32 + l;
 #pragma unroll
         for (int f = 0; f < S::REC_F4; ++f) cp_async16(dst + f * 32, src + f);
         cp_async_commit();
     };
-    if constexpr (S::REC_SMEM) issue(0);
+    if constexpr (S::REC_SMEM && NBUF == 2) issue(0);
     for (int ch = 0; ch < B / 64; ++ch) {
         float2 aj[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) aj[k] = f2(0.f, 0.f);
         if constexpr (S::REC_SMEM) {
-            if (ch + 1 < B / 64)
-                issue(ch + 1);
-            else
-                cp_async_commit();  // an empty group keeps "all but the newest" meaning chunk ch
-            cp_async_wait<1>();
+            if constexpr (NBUF == 2) {
+                if (ch + 1 < B / 64)
+                    issue(ch + 1);
+                else
+                    cp_async_commit();  // an empty group keeps "all but the newest" meaning chunk ch
+                cp_async_wait<1>();
+            } else {
+                issue(ch);
+                cp_async_wait<0>();
+            }
             __syncwarp();
-            const float4 *rb = rbw + (ch & 1) * S::REC_F4 * 32;
+            const float4 *rb = rbw + (ch % NBUF) * S::REC_F4 * 32;
             if (S::SELF_MASK && diag)
                 chunk_rounds_smem<S, true>(rb, si, ai, aj, c, l, next, i_base, ch * 64);
             else
                 chunk_rounds_smem<S, false>(rb, si, ai, aj, c, l, next, i_base, ch * 64);
-            __syncwarp();  // every lane is done with buffer ch & 1 before chunk ch + 2 refills it
+            __syncwarp();  // every lane is done with the buffer before it is refilled
         } else {
             const int64_t q = (int64_t)bj * (B / 2) + ch * 32 + l;  // this lane's record
             typename S::J sj;
@@ -805,7 +826,7 @@ cudaError_t launch_ex(const void *fn, dim3 grid, dim3 block, size_t smem, bool p
 template <class S, int W>
 constexpr size_t sym_smem() {
     return (size_t)W * S::NACC * (W * 32 * S::R) * 4 +
-           (S::REC_SMEM ? (size_t)W * 2 * S::REC_F4 * 32 * 16 : 0);
+           (S::REC_SMEM ? (size_t)W * rec_bufs<S, W>() * S::REC_F4 * 32 * 16 : 0);
 }
 
 template <class S, int W>
