@@ -18,12 +18,12 @@ namespace {
 // The plan's preset fields for these sizes: the tuned or pinned entry, else
 // the default shape, in FP32 in the pair-symmetric form when it needs less
 // than 0.85 of the one-sided form's FP32 work (groups of 256 bodies waste
-// little on systems of a few hundred bodies and more). The precision form
-// keeps the one-sided items unless pinned: the pair-symmetric items sum up to
-// 256 terms per FP32 partial against the one-sided tiles' 32 to 128, which
-// shows on close encounters (cube, eps = 0.01: positions after 4 steps
-// 4.4e-9 from the FP64 oracle against below 1e-9). Sizes whose partials
-// would exceed the single-system form's cap keep the one-sided items.
+// little on systems of a few hundred bodies and more). Untuned, the
+// precision form keeps the one-sided items: the pair-symmetric items sum up
+// to 256 terms per FP32 partial against the one-sided tiles' 32 to 128
+// (measured on 30 cube systems of 64 to 2048 bodies, eps = 0.01: 1.5e-11 in
+// x after 4 steps in both forms); the tuner times both. Sizes whose partials
+// would exceed kSymMaxPartBytes keep the one-sided items.
 void preset_plan(nb_ctx *ctx, const std::vector<int64_t> &off, BatchPlan &plan) {
     plan.f64 = f64_state(ctx) ? 1 : 0;
     auto tuned = ctx->batched_tuned.find(sizes_signature(off));
@@ -127,7 +127,7 @@ nb_status nb_autotune_batched(nb_ctx *ctx, int nsys, const int64_t *offsets) {
     for (const auto &shape : kShapes) {
         for (int jt : {64, 128}) {
             if (f64_state(ctx) && shape[1] > 4) continue;  // the precision form: R <= 4
-            if (shape[0] == 0 && (jt != 64 || f64_state(ctx))) continue;  // FP32 only (see preset_plan)
+            if (shape[0] == 0 && jt != 64) continue;  // the pair-symmetric form: its own shape
             BatchPlan plan;
             plan.f64 = f64_state(ctx) ? 1 : 0;
             plan.nt = shape[0];
