@@ -434,3 +434,31 @@ def test_sym_adjoint_precision_form_vs_fp64_oracle(nbm, vjp_block):
     errs = [rel_l2(to_np(g), r) for g, r in zip(got, ref)]
     print("precision-form adjoint, pair-symmetric kernels: %s" % ["%.2e" % e for e in errs])
     assert max(errs) <= 1e-6, errs
+
+
+def test_sym_tiled_adjoint_bit_identical(nbm):
+    """nb_adjoint with the forward recompute and the VJP launched by tiles
+    (the recompute on the adjoint's second stream with its own scratch)
+    gives the gradients of one launch per kernel bit for bit, in both
+    precisions."""
+    n, T, k = 3000, 12, 4
+    s = ics.cube(n, seed=23, masses="equal")
+    xstar = ics.targets(n, seed=23)
+    G, eps, dt = 1.0, 0.01, 1e-3
+    for prec, f in (("fp32", torch.float32), ("comp", torch.float64)):
+        grads = {}
+        for tile in (-1, 2):
+            ctx = nbm.Context(G, eps, dt, precision=prec)
+            ctx.debug_set(nbm.NB_DBG_FORM, 512)
+            ctx.debug_set(nbm.NB_DBG_VJP_FORM, 512)
+            ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+            ctx.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+            x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+            ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+            ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+            xbT = 2 * (x - _t(xstar, f))
+            g = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+            ctx.sync()
+            grads[tile] = [t.clone() for t in g]
+        for a, b in zip(grads[2], grads[-1]):
+            assert torch.equal(a, b), prec
