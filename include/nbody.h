@@ -37,7 +37,9 @@
  *   - The context owns all scratch memory (packed bodies, split partials,
  *     trajectory segments, CUDA graphs, tuning tables). It grows that memory
  *     on demand with cudaMalloc, outside any stream capture.
- *   - A context is not thread-safe; use one per host thread.
+ *   - A context is not thread-safe; use one per host thread. Its calls share
+ *     its scratch, so calls issued on different streams must not overlap on
+ *     the GPU: order the streams, or use one context per stream.
  *   - n == 0 is a valid no-op. No call aborts the process.
  */
 #ifndef NBODY_H

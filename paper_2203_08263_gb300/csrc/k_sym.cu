@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(32 * S::NACC) sym_finish_kernel(const ForceArg
     if (i < a.n) {
         const float *q = reinterpret_cast<const float *>(a.part) + (int64_t)k * a.npad + i;
         const int64_t stride = (int64_t)NA * a.npad;  // one partner block
-#pragma unroll 4
+#pragma unroll 16
         for (int p = 0; p < a.ntiles; ++p) {
             const float v = __ldcs(q + p * stride);
             if constexpr (S::COMP) {
