@@ -433,9 +433,11 @@ __device__ __forceinline__ void chunk_rounds_smem(const float4 *rb, const typena
 // Tiled launches: the partials of one tile, [slot][side][k][b] (slot = the
 // block pair's index in its tile, side 0 = the i side for block bi, 1 = the
 // j side for block bj, b = body within the block), and the partner range of
-// a block in a tile. tile_partner returns the first partner block and their
-// count for block `beta` (0 if the tile does not touch it); partner p's
-// partial is at slot tile_slot(g, beta, p) and side p < beta.
+// a block in a tile. tile_partners returns the number of partner blocks of
+// block `beta` in tile g (0 if the tile does not touch it) and sets the
+// first one; partner p's partial is on side 1 (p < beta: the j side of item
+// (p, beta)) at slot tile_slot(g, p, beta), else on side 0 at
+// tile_slot(g, beta, p).
 __device__ __forceinline__ int tile_partners(const SymTile &g, int beta, int &p0) {
     if (beta >= g.c0 && beta < g.c0 + g.hc) {  // column strip (and the diagonal tile's strip)
         p0 = g.r0;
@@ -456,7 +458,7 @@ __device__ __forceinline__ int tile_slot(const SymTile &g, int bi, int bj) {
     return (bi - g.r0) * g.hc + (bj - g.c0);
 }
 
-// Add tile `t`'s partials of body `o` of block `beta`, all NA sums, to the
+// Add tile g's partials of body `o` of block `beta`, all NA sums, to the
 // running sums (hi, lo) in partner order; the tile whose first partner is
 // block 0 starts them. FP32 sums, or two-sums in the precision form, as the
 // one-launch epilogue adds its partials.
@@ -478,8 +480,8 @@ __device__ __forceinline__ void tile_fold_body(const ForceArgs &a, const float *
             l[k] = S::COMP ? __ldcg(acc + (int64_t)(NA + k) * a.npad + b) : 0.f;
         }
     }
-    // partners in batches: the batch's loads are in flight together (the
-    // fold is bound by L2 round trips, not bytes), then added in order
+    // partners in batches: the batch's loads are issued together, then
+    // added in partner order
     constexpr int PB = NA <= 4 ? 8 : 4;
     for (int q0 = 0; q0 < np; q0 += PB) {
         float v[PB][NA];

@@ -91,9 +91,9 @@ __host__ __device__ inline SymTile sym_tile(int t, int nb, int w) {
 // partials for one launch over all block pairs; two tile buffers take at
 // most kSymTileBufBytes. Measured at N = 262144 (805 MB of partials in one
 // launch): 3.99e12 interactions/s in one launch, 3.94e12 by tiles of 24 to
-// 96 blocks; below the threshold the partials' footprint is not worth that
-// 1 %.
-constexpr size_t kSymTileAbove = (size_t)2 << 30;
+// 96 blocks; at N = 524288 (3.2 GB), 100 steps: 80,120 against 78,979
+// GFLOPS. Below the threshold the partials' footprint is not worth that 1 %.
+constexpr size_t kSymTileAbove = (size_t)4 << 30;
 constexpr size_t kSymTileBufBytes = (size_t)64 << 20;
 
 struct Shape {
