@@ -107,9 +107,15 @@ __device__ __forceinline__ void pair_item(const SymBatchArgs &a, const float4 *s
         mi[r] = dup(pget_cg(src, i, 3));
         ax[r] = ay[r] = az[r] = f2(0.f, 0.f);
     }
+    // each lane's record of chunk ch + 1 is loaded while chunk ch runs
+    const float4 *qsrc = src + 2 * ((int64_t)gj * (kGrp / 2) + lane);
+    float4 n0 = __ldcg(qsrc), n1 = __ldcg(qsrc + 1);
     for (int ch = 0; ch < kGrp / 64; ++ch) {
-        const int64_t q = (int64_t)gj * (kGrp / 2) + ch * 32 + lane;  // this lane's record
-        const float4 r0 = __ldcg(src + 2 * q), r1 = __ldcg(src + 2 * q + 1);
+        const float4 r0 = n0, r1 = n1;
+        if (ch + 1 < kGrp / 64) {
+            n0 = __ldcg(qsrc + 64 * (ch + 1));
+            n1 = __ldcg(qsrc + 64 * (ch + 1) + 1);
+        }
         float2 xj = f2(r0.x, r0.y), yj = f2(r0.z, r0.w), zj = f2(r1.x, r1.y), mj = f2(r1.z, r1.w);
         float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
 #pragma unroll 1
