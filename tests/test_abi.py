@@ -59,3 +59,22 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.nb_last_error(None) == b""
     lib.nb_destroy(None)
     assert lib.nb_batched_max_n() >= 8192
+
+
+def _header_enum(prefix):
+    text = open(os.path.join(ROOT, "include", "nbody.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    """Debug keys, force forms and statuses: the values the binding passes
+    and decodes are the header's."""
+    dbg = _header_enum("NB_DBG_")
+    assert dbg and all(getattr(nb, k) == v for k, v in dbg.items())
+    forms = _header_enum("NB_FORM_")
+    assert sorted(forms.values()) == sorted(nb.FORMS)
+    for k, v in forms.items():
+        assert nb.FORMS[v] == k[len("NB_FORM_"):].lower(), (k, nb.FORMS[v])
+    st = _header_enum("NB_ERR_")
+    assert all(getattr(nb, k) == v for k, v in st.items())
