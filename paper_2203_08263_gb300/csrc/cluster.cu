@@ -38,7 +38,8 @@ struct ClusterArgs {
     int ckpt_every;
     // grid form only
     float4 *xm0, *xm1;   // packed positions in global memory, [npad] each, double-buffered
-    unsigned *bar;       // grid barrier: arrivals, cumulative over the launch (zeroed before it)
+    unsigned *bar;       // grid barrier: [0] arrivals, cumulative over the launch; [1] CTAs done.
+                         // Both zero at the start of a launch; the last CTA to finish zeroes them
     int *err;
     uint64_t timeout_ns;
     int stall;           // timeout tests: CTA 0 never arrives, so every barrier wait runs out
@@ -390,6 +391,17 @@ __global__ void __launch_bounds__(NT, 1) cluster_run_kernel(const ClusterArgs a)
             vw[3 * io + c] = vs[c];
         }
     }
+    if constexpr (GRID) {
+        // Every CTA has passed its last barrier (or given up) before it counts
+        // itself done, so once all have, nobody reads the arrivals again: the
+        // last one zeroes both counters for the next launch (no memset launch
+        // per call). A CTA that gave up at a barrier still gets here.
+        __syncthreads();
+        if (threadIdx.x == 0 && atomicAdd(a.bar + 1, 1u) == gridDim.x - 1) {
+            atomicExch(a.bar, 0u);
+            atomicExch(a.bar + 1, 0u);
+        }
+    }
 }
 
 constexpr int kClusterThreads = 512;
@@ -543,8 +555,6 @@ cudaError_t launch_grid_run(int ctas, int64_t n, bool f64, void *x, void *v, con
     a.stall = stall;
     const size_t smem = (size_t)a.npad * 16;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);

@@ -452,12 +452,12 @@ nb_status run_device(nb_ctx *ctx, int64_t n, void *x, void *v, const void *m, in
         const size_t bytes = (size_t)size * slice * 16;
         NB_TRY(ensure(ctx, ctx->xm[0], bytes));
         NB_TRY(ensure(ctx, ctx->xm[1], bytes));
-        NB_TRY(ensure(ctx, ctx->gridbar, 256));
+        NB_TRY(ensure(ctx, ctx->gridbar, 256, true));  // the barrier's counters start at zero
         NB_CUDA(launch_grid_run(size, n, f64_state(ctx), x, v, m, steps, kdk_flag, eps2, ctx->p.G,
                                 ctx->p.dt, ckpt, ckpt_every, (float4 *)ctx->xm[0].p,
                                 (float4 *)ctx->xm[1].p, (unsigned *)ctx->gridbar.p, ctx->err_word,
                                 ctx->timeout_ns, (ctx->debug & kDbgStallProducer) ? 1 : 0, st));
-        ctx->launches += 2;  // the counter reset and the kernel
+        ctx->launches += 1;
         return NB_OK;
     }
     Shape s;

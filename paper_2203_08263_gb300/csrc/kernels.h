@@ -177,8 +177,9 @@ cudaError_t launch_cluster_run(int cluster, int64_t n, bool f64, void *x, void *
                                int ckpt_every, cudaStream_t st);
 // The same step loop on a cooperative grid of up to one CTA per SM: slices
 // written to a global double buffer (xm0, xm1: [npad] records each, npad =
-// ctas x slice), a bounded grid barrier per step (bar: one counter, zeroed
-// by the launch), all records reloaded into shared memory.
+// ctas x slice), a bounded grid barrier per step (bar: two counters, zero
+// before the first launch; each launch leaves them zero), all records
+// reloaded into shared memory.
 constexpr int64_t kGridMaxN = 8192;  // one replica of 128 KiB
 constexpr int64_t kGridDefaultN = 4096;
 constexpr int64_t kGridDefaultN64 = 8192;

@@ -44,8 +44,8 @@ def test_cluster_run_matches_oracle(nbm, path, n):
     before = ctx.launch_count
     ctx.run(x, v, m, steps)
     ctx.sync()
-    # all steps in one kernel (the grid form also resets its barrier counter)
-    assert ctx.launch_count - before == (1 if path == CLUSTER else 2)
+    # all steps in one kernel (the grid form's barrier counters reset themselves)
+    assert ctx.launch_count - before == 1
     xr, vr = oracle.run(s.x, s.v, s.m, 1.0, 0.01, 1e-3, steps)
     assert rel_l2(to_np(x), xr) <= 1e-5
     assert rel_l2(to_np(v), vr) <= 1e-4
@@ -87,9 +87,9 @@ def test_cluster_and_graph_paths_agree_with_checkpoints(nbm, fused):
 
 def test_default_path_choice(nbm):
     """Untuned, FP32: the cluster path up to n = 512 (one launch for all
-    steps), the grid form up to 4096 (a counter reset and one launch), the
-    graph path above (the pack and one force launch per step)."""
-    for n, launches in ((512, 1), (1024, 2), (4096, 2), (5000, 11)):
+    steps), the grid form up to 4096 (one launch), the graph path above (the
+    pack and one force launch per step)."""
+    for n, launches in ((512, 1), (1024, 1), (4096, 1), (5000, 11)):
         s = ics.cube(n, seed=3)
         ctx = nbm.Context(1.0, 0.01, 1e-3)
         want = "cluster" if n <= 512 else ("grid" if n <= 4096 else "graph")
@@ -163,7 +163,7 @@ def test_cluster_precision_form_matches_oracle(nbm, path, n):
 def test_default_path_choice_precision_form(nbm):
     """Untuned, the precision form takes the cluster path up to n = 512, the
     grid form up to 8192 and the graph path above."""
-    for n, launches in ((512, 1), (1024, 2), (8192, 2), (9000, 11)):
+    for n, launches in ((512, 1), (1024, 1), (8192, 1), (9000, 11)):
         s = ics.plummer(n, seed=5)
         ctx = nbm.Context(1.0, 0.05, 5e-4, precision="comp")
         x, v, m = _t64(s.x), _t64(s.v), _t64(s.m)
