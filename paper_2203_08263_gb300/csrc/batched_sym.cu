@@ -49,7 +49,7 @@ constexpr int kSymWarps = 4;  // warps per CTA
 constexpr int kHoldW = NB_SYMB_HOLD;  // items a warp may hold unstarted
 constexpr unsigned kNone = 0xFFFFFFFFu;
 #ifndef NB_SYMB_MINB
-#define NB_SYMB_MINB 3  // resident CTAs per SM the FP32 kernel's registers are sized for (4: 128 registers, 2.72e12 interactions/s on the 512-system ensemble against 2.94e12 at 3)
+#define NB_SYMB_MINB 3  // resident CTAs per SM the FP32 kernel's registers are sized for (4: 128 registers, 3.15e12 interactions/s on the 512-system ensemble against 3.37e12 at 3, even with the epilogue and diagonal items out of line and no record prefetch)
 #endif
 
 struct SymBatchArgs {
