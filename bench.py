@@ -199,6 +199,13 @@ STEP_TRAFFIC_BYTES = {
     (128, 8, 26, 256): 12.73e6 + 63.50e6,
     (256, 2, 16, 256): 10.96e6 + 21.27e6,
 }
+# The pair-symmetric kernel by tiles (above 512 MiB of one-launch partials),
+# by (shape, launches per step): DRAM bytes per step, summed over the step's
+# tile launches of the pair kernel, the final fold and the pack (one-pass
+# capture at N = 262144 as above).
+STEP_TRAFFIC_TILED = {
+    ((128, 8, 1, 1024), 68): 0.02e6 + 19.57e6,  # 66 tiles of 24 x 24 block pairs
+}
 
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # unit counts x maximum SM clock
@@ -212,7 +219,11 @@ KERNEL_NAME = {"f32x2": "force_kernel<AccelF32x2> (+ its 1-launch pack, <0.1% of
                "scalar": "force_kernel<AccelScalar> (+ its 1-launch pack)",
                "pair_symmetric": "sym_force_kernel (+ sym_finish_kernel, the fixed-order sum of the "
                                  "block-pair partials with the kick/drift epilogue, and the pack: "
-                                 "timed together, so the kernel's own rate is slightly higher)"}
+                                 "timed together, so the kernel's own rate is slightly higher)",
+               "pair_symmetric_tiled": "sym_force_kernel by tiles of block pairs (one launch per tile, "
+                                       "each folding the previous tile's partials into running sums) "
+                                       "+ sym_tile_final_kernel (the last fold with the kick/drift "
+                                       "epilogue) + the pack: timed together"}
 
 
 def fp32_peak_tflops(props, sm_max_mhz):
@@ -312,12 +323,20 @@ def run_ours(args):
     lane_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
     achieved = ops * inter / (ms_step / 1e3) / 1e12
     shape_key = (cfg["threads"], cfg["bodies_per_thread"], cfg["split"], cfg["jtile"])
-    traffic = STEP_TRAFFIC_BYTES.get(shape_key) if n == 262144 else None
+    per_step = round(launches / args.steps)
+    tiled = form == "pair_symmetric" and per_step > 3  # pack, the tiles, the final fold
+    if tiled:
+        traffic = STEP_TRAFFIC_TILED.get((shape_key, per_step)) if n == 262144 else None
+        traffic_unit = (f"bytes per step ({per_step - 2} tile launches of the pair kernel, "
+                        "the final fold and the pack)")
+    else:
+        traffic = STEP_TRAFFIC_BYTES.get(shape_key) if n == 262144 else None
+        traffic_unit = "bytes per launch"
     roofline = {"bound": "alu", "achieved": achieved, "peak": lane_peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / lane_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "frac": achieved / lane_peak, "traffic": traffic, "traffic_unit": traffic_unit,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                               f"(max SM clock); {ops} lane operations per interaction in the {form} form",
-                "kernel": KERNEL_NAME.get(form, form),
+                "kernel": KERNEL_NAME.get(form + ("_tiled" if tiled else ""), form),
                 "pct_fp32_peak_20flop": 100.0 * FLOPS_PER_INTERACTION * inter / (ms_step / 1e3) / 1e12 / peak_20,
                 "pct_basis": f"20 flops per interaction (Section 4.1) over {peak_20:.2f} TFLOP/s "
                              "(2 flops per FMA lane); above the one-sided form's 83.3 % ceiling when "

@@ -121,12 +121,13 @@ nb_status nb_set_params(nb_ctx *ctx, double G, double eps, double dt);
  * form with FP32 pair terms and the partials two-summed before the FP64
  * update. One launch keeps nb x 3 x npad floats of partials in the context
  * (nb = npad / B blocks of B = 256, 512 or 1024 bodies, npad = n rounded up to a
- * block: about 12 n^2 / 1024 bytes, 0.8 GB at n = 262144). Above 4 GiB of
- * such partials (n = 2^20: 12.9 GB) the pair kernel is launched tile by tile
- * over w x w block pairs, each tile's partials folded into running sums in
- * the same order, with two tile buffers of at most 64 MiB and the running
- * sums (2 x 3 x npad floats): no size limit, bit-identical results, about
- * 1 % slower. The VJP of nb_vjp and nb_adjoint (FP32 and the precision form)
+ * block: about 12 n^2 / 1024 bytes, 0.2 GB at n = 131072). Above 512 MiB
+ * of such partials (n = 262144: 0.8 GB; n = 2^20: 12.9 GB) the pair kernel
+ * is launched tile by tile over w x w block pairs, each tile's partials
+ * folded into running sums in the same order, with two tile buffers of at
+ * most 28 MiB in all and the running sums (2 x 3 x npad floats): no size
+ * limit, bit-identical results, the same speed. The VJP of nb_vjp and
+ * nb_adjoint (FP32 and the precision form)
  * has the same forms (the pair-symmetric one from n = 8192, blocks of 256 or
  * 512 bodies, 8 sums per body: about 32 n^2 / 256 bytes in one launch at
  * n < 65536). Results are deterministic in every form.
@@ -345,9 +346,10 @@ typedef enum {
      * pair-symmetric kernel with blocks of that many bodies at every size. */
     NB_DBG_VJP_FORM = 6,
     /* Pair-symmetric launches (forces, precision form, VJP): 0 = chosen per
-     * size (default: one launch over all block pairs up to 4 GiB of
+     * size (default: one launch over all block pairs up to 512 MiB of
      * partials, above that one launch per tile of w x w block pairs with a
-     * running sum of the partials, two tile buffers of at most 64 MiB), -1 =
+     * running sum of the partials, two tile buffers of at most 28 MiB in
+     * all), -1 =
      * one launch always, w > 0 = tiles of w blocks whenever that makes more
      * than one tile. Results are bit-identical either way. */
     NB_DBG_SYM_TILE = 7

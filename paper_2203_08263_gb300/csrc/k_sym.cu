@@ -66,6 +66,7 @@ struct SymAccel {
     static constexpr int NACC = 3;      // a_x, a_y, a_z
     static constexpr int REC_F4 = 2;    // {x0,x1,y0,y1} {z0,z1,m0,m1}
     static constexpr bool SELF_MASK = false;  // d = 0 gives exactly 0
+    static constexpr bool BLOCK_CALL = true;
     __host__ __device__ static constexpr float jsign(int) { return -1.f; }
     struct I { float2 nx, ny, nz, m; };
     struct J { float2 x, y, z, m; };
@@ -163,6 +164,7 @@ struct SymVjp {
     static constexpr int NACC = 8;
     static constexpr int REC_F4 = 4;
     static constexpr bool SELF_MASK = true;
+    static constexpr bool BLOCK_CALL = false;
     // j side: U as is; V gathered with -m_i; W and P with the sign flipped
     __host__ __device__ static constexpr float jsign(int k) { return k < 3 ? 1.f : -1.f; }
     struct I { float2 nx, ny, nz, nm, ax, ay, az; };  // nm = -m_i
@@ -281,6 +283,7 @@ struct SymVjpComp {
     static constexpr int NACC = 8;
     static constexpr int REC_F4 = 5;
     static constexpr bool SELF_MASK = true;
+    static constexpr bool BLOCK_CALL = false;
     __host__ __device__ static constexpr float jsign(int k) { return SymVjp::jsign(k); }
     struct I {
         SymVjp::I b;
@@ -587,38 +590,24 @@ __host__ __device__ constexpr int rec_bufs() {
 }
 
 
-// TILED: one launch per tile (the launch's tile and its fold of the previous
-// tile); otherwise one launch over every block pair. Two instances, so that
-// the tile code does not change the code of the one-launch kernel.
-template <class S, int W, bool TILED>
-__global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(const ForceArgs a) {
+// The pair work of block pair (bi, bj) and its partials: the i side's NA sums
+// of the bodies of block bi to pi[k * ps + o] and the j side's of block bj to
+// pj[k * ps + o] (o = the body's offset in its block). late_wait: wait for
+// the previous grid before the first write (tile launches). For the forces
+// (S::BLOCK_CALL) the two kernels call it out of line, so that the one-launch
+// and the tile kernels run the same compiled pair loop: inlined into each,
+// the tile kernel's copy ran 0.8 % slower (3.94e12 against 3.99e12
+// interactions/s at N = 262144 with tiles of 24 to 96 blocks, 3.97e12
+// against 4.02e12 for the precision form at N = 2^20). The VJPs' one-launch
+// kernel keeps it inlined (out of line, the N = 16384 adjoint took 47.0
+// against 46.8 ms) and their tile kernel calls it out of line (10.07 ms per
+// VJP at N = 131072 by tiles of 20 blocks, against 10.15 inlined and 10.10
+// in one launch).
+template <class S, int W>
+__device__ __forceinline__ void sym_block_body(const ForceArgs &a, int bi, int bj, float *pi, float *pj,
+                                               int64_t ps, bool late_wait) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
     extern __shared__ float acc_j[];  // [W][NA][B]
-    // the previous step's epilogue (it reads the partials and writes the
-    // records read here) must be complete: the first (or only) launch of a
-    // step waits for it; a later tile launch starts early, its records
-    // written before the step's first tile began, and waits below before
-    // it writes partials
-    if (!TILED || a.tile == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
-    // tiles: the next tile's CTAs may take the SMs this launch's last wave
-    // leaves (each waits for this grid before writing anything)
-    if constexpr (TILED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int nb = (int)(a.npad / B);
-    int bi, bj;
-    if constexpr (TILED) {
-        const SymTile g = sym_tile(a.tile, nb, a.tile_w);
-        if (g.I == g.J) {
-            int r, cc;
-            tri_item(blockIdx.x, g.hr, r, cc);
-            bi = g.r0 + r;
-            bj = g.r0 + cc;
-        } else {
-            bi = g.r0 + (int)(blockIdx.x / g.hc);
-            bj = g.c0 + (int)(blockIdx.x % g.hc);
-        }
-    } else {
-        sym_item(blockIdx.x, nb, bi, bj);
-    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int next = (l + 1) & 31;
     typename S::C c;
@@ -689,58 +678,82 @@ __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(c
             }
         }
     }
+    if (late_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < NA; ++k) __stcg(pi + k * ps + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
+    if (!diag) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < B; t += W * 32) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
+                __stcg(pj + k * ps + t, s);
+            }
+        }
+    }
+}
+
+template <class S, int W>
+__device__ __noinline__ void sym_block_call(const ForceArgs &a, int bi, int bj, float *pi, float *pj, int64_t ps,
+                                            bool late_wait) {
+    sym_block_body<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+}
+template <class S, int W, bool TILED>
+__device__ __forceinline__ void sym_block(const ForceArgs &a, int bi, int bj, float *pi, float *pj, int64_t ps,
+                                          bool late_wait) {
+    if constexpr (S::BLOCK_CALL || TILED)
+        sym_block_call<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+    else
+        sym_block_body<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+}
+
+// TILED: one launch per tile (the launch's tile and its fold of the previous
+// tile); otherwise one launch over every block pair. Both run sym_block.
+template <class S, int W, bool TILED>
+__global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(const ForceArgs a) {
+    constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
+    // the previous step's epilogue (it reads the partials and writes the
+    // records read here) must be complete: the first (or only) launch of a
+    // step waits for it; a later tile launch starts early, its records
+    // written before the step's first tile began, and waits in sym_block
+    // before it writes partials
+    if (!TILED || a.tile == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
+    // tiles: the next tile's CTAs may take the SMs this launch's last wave
+    // leaves (each waits for this grid before writing anything)
+    if constexpr (TILED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int nb = (int)(a.npad / B);
     float *P = reinterpret_cast<float *>(a.part);
+    int bi, bj;
     if constexpr (TILED) {
-        // the previous tile's grid is complete: its partials are final for
-        // the fold below, and this buffer (the tile before it) is folded;
-        // this item's partials go to its slot of the buffer
-        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const SymTile g = sym_tile(a.tile, nb, a.tile_w);
+        if (g.I == g.J) {
+            int r, cc;
+            tri_item(blockIdx.x, g.hr, r, cc);
+            bi = g.r0 + r;
+            bj = g.r0 + cc;
+        } else {
+            bi = g.r0 + (int)(blockIdx.x / g.hc);
+            bj = g.c0 + (int)(blockIdx.x % g.hc);
+        }
+        // this item's slot of the tile buffer: [side][k][b], side 0 for block bi
         float *pi = P + (a.tile & 1) * tile_buf_floats<S, B>(a.tile_w) + ((int64_t)blockIdx.x * 2) * NA * B;
-        float *pj = pi + NA * B;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int k = 0; k < NA; ++k) __stcg(pi + k * B + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
-        if (!diag) {
-            __syncthreads();
-            for (int t = threadIdx.x; t < B; t += W * 32) {
-#pragma unroll
-                for (int k = 0; k < NA; ++k) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
-                    __stcg(pj + k * B + t, s);
-                }
-            }
-        }
+        sym_block<S, W, true>(a, bi, bj, pi, pi + NA * B, B, true);
+        // the previous tile's grid is complete (waited for in sym_block): its
+        // partials are final for the fold, and this buffer (the tile before
+        // it) is folded
+        if (a.tile > 0) tile_fold_prev<S, W>(a);
     } else {
+        sym_item(blockIdx.x, nb, bi, bj);
         const int64_t np = a.npad;
-        {
-            float *p = P + (int64_t)bj * NA * np + gbase;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int k = 0; k < NA; ++k) __stcg(p + k * np + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
-        }
-        if (!diag) {
-            __syncthreads();
-            float *p = P + (int64_t)bi * NA * np + (int64_t)bj * B;
-            for (int t = threadIdx.x; t < B; t += W * 32) {
-#pragma unroll
-                for (int k = 0; k < NA; ++k) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int u = 0; u < W; ++u) s += acc_j[(u * NA + k) * B + t];
-                    __stcg(p + k * np + t, s);
-                }
-            }
-        }
-    }
-    if constexpr (!TILED) {
+        // P[p][k][b]: row bj for block bi's bodies, row bi for block bj's
+        sym_block<S, W, false>(a, bi, bj, P + (int64_t)bj * NA * np + (int64_t)bi * B,
+                        P + (int64_t)bi * NA * np + (int64_t)bj * B, np, false);
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-        return;
     }
-    if (a.tile > 0) tile_fold_prev<S, W>(a);
 }
 
 // Sum of the nb partials of each body in block order (the policy's Fin:

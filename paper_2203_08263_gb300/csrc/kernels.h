@@ -89,12 +89,26 @@ __host__ __device__ inline SymTile sym_tile(int t, int nb, int w) {
 }
 // Tiles of the pair-symmetric forms are used above this many bytes of
 // partials for one launch over all block pairs; two tile buffers take at
-// most kSymTileBufBytes. Measured at N = 262144 (805 MB of partials in one
-// launch): 3.99e12 interactions/s in one launch, 3.94e12 by tiles of 24 to
-// 96 blocks; at N = 524288 (3.2 GB), 100 steps: 80,120 against 78,979
-// GFLOPS. Below the threshold the partials' footprint is not worth that 1 %.
-constexpr size_t kSymTileAbove = (size_t)4 << 30;
-constexpr size_t kSymTileBufBytes = (size_t)64 << 20;
+// most kSymTileBufBytes. With the one-launch and the tile kernels running
+// the same compiled pair loop, tiles cost nothing measurable: at N = 262144
+// (805 MB of partials in one launch) 3.987e12 interactions/s in one launch
+// against 3.984e12-3.991e12 by tiles of 16 to 49 blocks (3 steps per call),
+// and 17.234 ms per bench step in one launch against 17.229 by tiles of 49;
+// at N = 524288 4.009e12 against 4.017e12; at N = 131072 (201 MB, below the
+// threshold) 3.916e12 against 3.908e12. The buffers' bound sets the tile
+// side, and small tiles keep both buffers in L2: DRAM bytes written per
+// N = 262144 step are 8 / 20 / 84 / 380 / 687 MB with tiles of 20 / 24 / 28 /
+// 36 / 49 blocks (buffers of 19 / 28 / 38 / 62 / 118 MB), 774 MB in one
+// launch, whose epilogue also reads 749 MB back. 28 MiB gives tiles of 24
+// blocks for the forces (1024-body blocks) and of 20 for the VJP (512).
+#ifndef NB_SYM_TILE_ABOVE_MIB
+#define NB_SYM_TILE_ABOVE_MIB 512
+#endif
+#ifndef NB_SYM_TILE_BUF_MIB
+#define NB_SYM_TILE_BUF_MIB 28
+#endif
+constexpr size_t kSymTileAbove = (size_t)NB_SYM_TILE_ABOVE_MIB << 20;
+constexpr size_t kSymTileBufBytes = (size_t)NB_SYM_TILE_BUF_MIB << 20;
 
 struct Shape {
     int pol, nt, r, split, jt;

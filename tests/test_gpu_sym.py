@@ -357,10 +357,10 @@ def test_sym_tiled_launches_bit_identical(nbm, w):
 
 
 def test_sym_tiles_by_default_at_large_n(nbm):
-    """Above 4 GiB of partials for one launch the forces go by tiles: at
-    N = 786432 (1024-body blocks, 7.2 GB of partials in one launch) a step is
+    """Above 512 MiB of partials for one launch the forces go by tiles: at
+    N = 262144 (1024-body blocks, 0.8 GB of partials in one launch) a step is
     the pack, one launch per tile and the final sum."""
-    n = 786432
+    n = 262144
     ctx = nbm.Context(1.0, 0.05, 1e-3)
     if ctx.get_config(n)["tuned"]:
         pytest.skip("a tuning table is loaded")
