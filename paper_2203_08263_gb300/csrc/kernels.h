@@ -100,7 +100,7 @@ __host__ __device__ inline SymTile sym_tile(int t, int nb, int w) {
 // N = 262144 step are 8 / 20 / 84 / 380 / 687 MB with tiles of 20 / 24 / 28 /
 // 36 / 49 blocks (buffers of 19 / 28 / 38 / 62 / 118 MB), 774 MB in one
 // launch, whose epilogue also reads 749 MB back. 28 MiB gives tiles of 24
-// blocks for the forces (1024-body blocks) and of 20 for the VJP (512).
+// blocks for the forces (1024-body blocks) and of 21 for the VJP (512).
 #ifndef NB_SYM_TILE_ABOVE_MIB
 #define NB_SYM_TILE_ABOVE_MIB 512
 #endif
