@@ -8,8 +8,10 @@
 // block-pair partials, and an epilogue item (s, g) adds group g's partials in
 // group order and runs the update (half kick, drift, repack; the precision
 // form two-sums the partials and updates in FP64). Items are numbered
-// step-major; within a step all pair items (largest systems first) precede
-// all epilogue items. A pair item of step t waits for every epilogue item of
+// step-major; within a step the pair items come largest systems first, and
+// each system's epilogue items follow its last pair item after a lag of
+// about five times the grid's warps (in items), or at the step's end. A pair
+// item of step t waits for every epilogue item of
 // step t-1 of its system (the positions it reads), an epilogue item for every
 // pair item of step t of its system (the partials it reads); both are lower
 // numbers, so the oldest unfinished item is always ready and the queue always
@@ -51,6 +53,15 @@ constexpr int kSymWarps = 4;  // warps per CTA
 #endif
 constexpr int kHoldW = NB_SYMB_HOLD;  // items a warp may hold unstarted
 constexpr unsigned kNone = 0xFFFFFFFFu;
+#ifndef NB_SYMB_EPI_LAG
+// measured on the 512-system ensemble (1,824 warps, 29,917 items per step):
+// 3.37e12 interactions/s with every epilogue item after every pair item (0);
+// 3.02e12 / 3.11e12 / 3.26e12 at lags of 0.5 / 1 / 2 grid-warps of items
+// (epilogue items taken while their system's pair items still run wait for
+// them), 3.37e12 at 3, 3.42e12 at 4 to 6, 3.41e12 at 8 and 11 (the partials
+// read soon after they were written, from L2)
+#define NB_SYMB_EPI_LAG 5.0
+#endif
 #ifndef NB_SYMB_MINB
 #define NB_SYMB_MINB 3  // resident CTAs per SM the FP32 kernel's registers are sized for (4: 128 registers, 3.15e12 interactions/s on the 512-system ensemble against 3.37e12 at 3, even with the epilogue and diagonal items out of line and no record prefetch)
 #endif
@@ -610,17 +621,35 @@ bool batched_sym_plan(int num_sms, const std::vector<int64_t> &off, BatchPlan &p
     }
     p.total_pad = std::max<int64_t>(acc, kGrp);
     p.sym_part_floats = std::max<int64_t>(pacc, 1);
-    // a step: pair items of the largest systems first, then every epilogue item
+    // a step: pair items of the largest systems first; each system's epilogue
+    // items follow its last pair item after a lag of about NB_SYMB_EPI_LAG x
+    // the grid's warps (0: all epilogue items after all pair items), in the
+    // same system order, so the next step's first pair items (the largest
+    // systems') become ready first
     std::stable_sort(pairs.begin(), pairs.end(), [](const Pair &x, const Pair &y) { return x.g > y.g; });
-    p.sym_items.clear();
-    for (const Pair &q : pairs) p.sym_items.insert(p.sym_items.end(), {q.s, q.gi, q.gj, 0});
-    // epilogue items in the same system order, so the next step's first pair
-    // items (the largest systems') become ready first
     std::vector<int> order(p.nsys);
     for (int s = 0; s < p.nsys; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p.sym_ng[x] > p.sym_ng[y]; });
-    for (int s : order)
+    int64_t nepi = 0;
+    for (int s = 0; s < p.nsys; ++s) nepi += p.sym_ng[s];
+    const int64_t nwarps =
+        std::min<int64_t>((int64_t)occ * num_sms, ((int64_t)pairs.size() + nepi + kSymWarps - 1) / kSymWarps) *
+        kSymWarps;
+    const int64_t lag = (int64_t)(NB_SYMB_EPI_LAG * (double)nwarps);
+    std::vector<int64_t> last(p.nsys, -1);  // each system's last pair item
+    for (size_t k = 0; k < pairs.size(); ++k) last[pairs[k].s] = (int64_t)k;
+    p.sym_items.clear();
+    size_t next_epi = 0;  // systems in `order` whose epilogue items are out
+    auto emit_epi = [&](int s) {
         for (int g = 0; g < p.sym_ng[s]; ++g) p.sym_items.insert(p.sym_items.end(), {s, g, 0, 1});
+    };
+    for (size_t k = 0; k < pairs.size(); ++k) {
+        const Pair &q = pairs[k];
+        p.sym_items.insert(p.sym_items.end(), {q.s, q.gi, q.gj, 0});
+        if (NB_SYMB_EPI_LAG > 0)
+            while (next_epi < order.size() && last[order[next_epi]] + lag <= (int64_t)k) emit_epi(order[next_epi++]);
+    }
+    while (next_epi < order.size()) emit_epi(order[next_epi++]);
     p.items_per_step = (int)(p.sym_items.size() / 4);
     p.ncta = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)occ * num_sms, (p.items_per_step + kSymWarps - 1) / kSymWarps));
