@@ -50,7 +50,10 @@ def sweep(steps: int, nmax: int):
             ctx = Context(1.0, 0.05, 1e-3, precision=prec)
             ctx.autotune(n)  # launch shape and nb_run path for this size
             x, v, m = (torch.tensor(a, dtype=f, device=dev) for a in (s.x, s.v, s.m))
-            ctx.run(x.clone(), v.clone(), m, steps)  # capture the graph
+            x0, v0 = x.clone(), v.clone()
+            ctx.run(x, v, m, steps)  # the timed call once: its step graph is captured here
+            x.copy_(x0)
+            v.copy_(v0)
             t = _timed(torch, lambda: ctx.run(x, v, m, steps))
             ctx.sync()
             row[prec] = {"s": t, "gflops": 20.0 * n * n * steps / t / 1e9,
