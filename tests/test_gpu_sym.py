@@ -321,8 +321,9 @@ def test_sym_tiled_launches_bit_identical(nbm, w):
     """The pair-symmetric kernels launched tile by tile (w x w block pairs per
     launch, the partials of each tile folded into running sums in partner
     order) give bit for bit the results of one launch over all block pairs:
-    forces, a run, the precision form and the VJP, with ragged last strips
-    (20 blocks of 1024 bodies; 35 of 512 for the VJP)."""
+    forces, runs of both schemes (the precision form's with checkpoints), the
+    precision form and the VJP, with ragged last strips (20 blocks of 1024
+    bodies; 35 of 512 for the VJP)."""
     n = 20000
     s = ics.plummer(n, seed=31)
     G, eps = 1.0, 0.05
@@ -346,10 +347,21 @@ def test_sym_tiled_launches_bit_identical(nbm, w):
         comp = nbm.Context(G, eps, 1e-3, precision="comp")
         comp.debug_set(nbm.NB_DBG_FORM, 1024)
         comp.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+        comp.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
         ac = comp.accel(_t(s.x, torch.float64), _t(s.m, torch.float64))
+        xc, vc = _t(s.x, torch.float64), _t(s.v, torch.float64)
+        ck = torch.zeros((3, n, 6), dtype=torch.float64, device="cuda")
+        comp.run(xc, vc, _t(s.m, torch.float64), 4, ckpt=ck, ckpt_every=2)
+        kdk = nbm.Context(G, eps, 1e-3, scheme="kdk")
+        kdk.debug_set(nbm.NB_DBG_FORM, 1024)
+        kdk.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+        kdk.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+        xk, vk = _t(s.x), _t(s.v)
+        kdk.run(xk, vk, _t(s.m), 4)
         ctx.sync()
         comp.sync()
-        out[tile] = [t.clone() for t in (a, x, v, xb, mb, ac)]
+        kdk.sync()
+        out[tile] = [t.clone() for t in (a, x, v, xb, mb, ac, xc, vc, ck, xk, vk)]
     for got, ref in zip(out[w], out[-1]):
         assert torch.equal(got, ref)
     assert rel_l2(to_np(out[w][0]), oracle.accel(s.x, s.m, G, eps)) <= 2e-5
