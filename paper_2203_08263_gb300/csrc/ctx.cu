@@ -197,10 +197,14 @@ Shape heuristic_shape(const nb_ctx *ctx, int mode, int64_t n, bool allow_sym) {
     int nt = 128, r = 1, jt = 64;
     if ((pol == kPolF32x2 || pol == kPolComp) && allow_sym && n >= 16384) {
         // each unordered pair once, blocks of 1024 bodies from 2^17 up (enough
-        // block pairs to fill the GPU), 512 below
+        // block pairs to fill the GPU), 512 below, and below 2^15 blocks of
+        // 256 whose block pairs two warps share (64 threads x kSymR / 2: more
+        // resident warps where the block pairs are few)
+        const int sp = pol == kPolComp ? kPolSymComp : kPolSym;
+        if (n < 32768) return Shape{sp, 64, kSymR / 2, 1, 64 * (kSymR / 2)};
         const int snt = n >= 131072 ? 128 : 64;
         const int64_t b = (int64_t)snt * kSymR;
-        return Shape{pol == kPolComp ? kPolSymComp : kPolSym, snt, kSymR, 1, (int)b};
+        return Shape{sp, snt, kSymR, 1, (int)b};
     }
     if (pol == kPolF32x2) {
         if (n >= 32768) { r = 4; jt = 128; }

@@ -539,12 +539,19 @@ __host__ __device__ constexpr int64_t tile_buf_floats(int w) {
     return (int64_t)w * w * 2 * S::NACC * B;
 }
 
-// Fold the previous tile into the running sums: units of W x 32 bodies of
-// the blocks it touched (its row strip, then its column strip), one body per
-// thread, spread over this launch's CTAs. Not inlined: the pair loop before
+// Threads per CTA: W i-warps, each with JS warps that hold the same i-bodies
+// and split the block pair's j-chunks between them (JS > 1: the forces).
+template <int W, int JS>
+__host__ __device__ constexpr int sym_threads() {
+    return W * 32 * JS;
+}
+
+// Fold the previous tile into the running sums: units of one body per
+// thread of the blocks it touched (its row strip, then its column strip),
+// spread over this launch's CTAs. Not inlined: the pair loop before
 // the call keeps all the registers (inlined, this code cost the loop 2.6 %
 // at N = 262144 without ever running).
-template <class S, int W>
+template <class S, int W, int JS>
 __device__ __noinline__ void tile_fold_prev(const ForceArgs &a) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
     const int nb = (int)(a.npad / B);
@@ -553,11 +560,12 @@ __device__ __noinline__ void tile_fold_prev(const ForceArgs &a) {
     const float *pbuf = P + ((a.tile - 1) & 1) * tile_buf_floats<S, B>(a.tile_w);
     float *acc = P + 2 * tile_buf_floats<S, B>(a.tile_w);
     const int nblk = pg.I == pg.J ? pg.hr : pg.hr + pg.hc;
-    constexpr int kUnits = B / (W * 32);  // units per block
+    constexpr int NT = sym_threads<W, JS>();
+    constexpr int kUnits = B / NT;  // units per block
     for (int u = blockIdx.x; u < nblk * kUnits; u += gridDim.x) {
         const int kb = u / kUnits;
         const int beta = kb < pg.hr ? pg.r0 + kb : pg.c0 + (kb - pg.hr);
-        const int o = (u % kUnits) * (W * 32) + threadIdx.x;
+        const int o = (u % kUnits) * NT + threadIdx.x;
         float h[NA], lo[NA];
         tile_fold_body<S, B>(a, acc, pbuf, pg, beta, o, h, lo);
         const int64_t b = (int64_t)beta * B + o;
@@ -572,9 +580,9 @@ __device__ __noinline__ void tile_fold_prev(const ForceArgs &a) {
 // Resident CTAs per SM that keep a policy's registers at its target (the
 // compiler's own choice without a bound; a bound of 1 CTA let it take 210 for
 // the VJP).
-template <class S, int W>
+template <class S, int W, int JS = 1>
 __host__ __device__ constexpr int sym_min_blocks() {
-    return 65536 / (W * 32 * S::REGS) > 0 ? 65536 / (W * 32 * S::REGS) : 1;
+    return 65536 / (sym_threads<W, JS>() * S::REGS) > 0 ? 65536 / (sym_threads<W, JS>() * S::REGS) : 1;
 }
 
 // Record buffers per warp of the staged-record kernels: two unless the
@@ -603,12 +611,16 @@ __host__ __device__ constexpr int rec_bufs() {
 // against 46.8 ms) and their tile kernel calls it out of line (10.07 ms per
 // VJP at N = 131072 by tiles of 20 blocks, against 10.15 inlined and 10.10
 // in one launch).
-template <class S, int W>
+template <class S, int W, int JS>
 __device__ __forceinline__ void sym_block_body(const ForceArgs &a, int bi, int bj, float *pi, float *pj,
                                                int64_t ps, bool late_wait) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
-    extern __shared__ float acc_j[];  // [W][NA][B]
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    constexpr int NT = sym_threads<W, JS>(), C = B / 64 / JS;  // chunks per warp
+    static_assert(!(S::REC_SMEM && JS > 1), "split j-chunks with records by shuffle only");
+    extern __shared__ float acc_j[];  // [W][NA][B], then with JS > 1 [JS - 1][R][NA][32]
+    const int w = JS > 1 ? (threadIdx.x >> 5) % W : threadIdx.x >> 5;  // the i-warp
+    const int js = JS > 1 ? (threadIdx.x >> 5) / W : 0;                 // its share of the chunks
+    const int l = threadIdx.x & 31;
     const int next = (l + 1) & 31;
     typename S::C c;
     S::consts(a, c);
@@ -638,7 +650,7 @@ __device__ __forceinline__ void sym_block_body(const ForceArgs &a, int bi, int b
         cp_async_commit();
     };
     if constexpr (S::REC_SMEM && NBUF == 2) issue(0);
-    for (int ch = 0; ch < B / 64; ++ch) {
+    for (int ch = js * C; ch < (js + 1) * C; ++ch) {
         float2 aj[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) aj[k] = f2(0.f, 0.f);
@@ -679,13 +691,37 @@ __device__ __forceinline__ void sym_block_body(const ForceArgs &a, int bi, int b
         }
     }
     if (late_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if constexpr (JS > 1) {
+        // the i side: the j-split warps' sums of the same bodies, added in
+        // warp order by the first
+        float *xs = acc_j + W * NA * B;
+        if (js > 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < NA; ++k) __stcg(pi + k * ps + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
+                for (int k = 0; k < NA; ++k) xs[(((js - 1) * R + r) * NA + k) * 32 + l] = ai[r][k].x + ai[r][k].y;
+        }
+        __syncthreads();
+        if (js == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    float v = ai[r][k].x + ai[r][k].y;
+#pragma unroll
+                    for (int q = 1; q < JS; ++q) v += xs[(((q - 1) * R + r) * NA + k) * 32 + l];
+                    __stcg(pi + k * ps + i_base + 32 * r, v);
+                }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < NA; ++k) __stcg(pi + k * ps + i_base + 32 * r, ai[r][k].x + ai[r][k].y);
+    }
     if (!diag) {
         __syncthreads();
-        for (int t = threadIdx.x; t < B; t += W * 32) {
+        for (int t = threadIdx.x; t < B; t += NT) {
 #pragma unroll
             for (int k = 0; k < NA; ++k) {
                 float s = 0.f;
@@ -697,24 +733,24 @@ __device__ __forceinline__ void sym_block_body(const ForceArgs &a, int bi, int b
     }
 }
 
-template <class S, int W>
+template <class S, int W, int JS>
 __device__ __noinline__ void sym_block_call(const ForceArgs &a, int bi, int bj, float *pi, float *pj, int64_t ps,
                                             bool late_wait) {
-    sym_block_body<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+    sym_block_body<S, W, JS>(a, bi, bj, pi, pj, ps, late_wait);
 }
-template <class S, int W, bool TILED>
+template <class S, int W, int JS, bool TILED>
 __device__ __forceinline__ void sym_block(const ForceArgs &a, int bi, int bj, float *pi, float *pj, int64_t ps,
                                           bool late_wait) {
     if constexpr (S::BLOCK_CALL || TILED)
-        sym_block_call<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+        sym_block_call<S, W, JS>(a, bi, bj, pi, pj, ps, late_wait);
     else
-        sym_block_body<S, W>(a, bi, bj, pi, pj, ps, late_wait);
+        sym_block_body<S, W, JS>(a, bi, bj, pi, pj, ps, late_wait);
 }
 
 // TILED: one launch per tile (the launch's tile and its fold of the previous
 // tile); otherwise one launch over every block pair. Both run sym_block.
-template <class S, int W, bool TILED>
-__global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(const ForceArgs a) {
+template <class S, int W, int JS, bool TILED>
+__global__ void __launch_bounds__(sym_threads<W, JS>(), (sym_min_blocks<S, W, JS>())) sym_kernel(const ForceArgs a) {
     constexpr int R = S::R, B = W * 32 * R, NA = S::NACC;
     // the previous step's epilogue (it reads the partials and writes the
     // records read here) must be complete: the first (or only) launch of a
@@ -741,16 +777,16 @@ __global__ void __launch_bounds__(W * 32, (sym_min_blocks<S, W>())) sym_kernel(c
         }
         // this item's slot of the tile buffer: [side][k][b], side 0 for block bi
         float *pi = P + (a.tile & 1) * tile_buf_floats<S, B>(a.tile_w) + ((int64_t)blockIdx.x * 2) * NA * B;
-        sym_block<S, W, true>(a, bi, bj, pi, pi + NA * B, B, true);
+        sym_block<S, W, JS, true>(a, bi, bj, pi, pi + NA * B, B, true);
         // the previous tile's grid is complete (waited for in sym_block): its
         // partials are final for the fold, and this buffer (the tile before
         // it) is folded
-        if (a.tile > 0) tile_fold_prev<S, W>(a);
+        if (a.tile > 0) tile_fold_prev<S, W, JS>(a);
     } else {
         sym_item(blockIdx.x, nb, bi, bj);
         const int64_t np = a.npad;
         // P[p][k][b]: row bj for block bi's bodies, row bi for block bj's
-        sym_block<S, W, false>(a, bi, bj, P + (int64_t)bj * NA * np + (int64_t)bi * B,
+        sym_block<S, W, JS, false>(a, bi, bj, P + (int64_t)bj * NA * np + (int64_t)bi * B,
                         P + (int64_t)bi * NA * np + (int64_t)bj * B, np, false);
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
@@ -852,18 +888,19 @@ cudaError_t launch_ex(const void *fn, dim3 grid, dim3 block, size_t smem, bool p
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template <class S, int W>
+template <class S, int W, int JS>
 constexpr size_t sym_smem() {
     return (size_t)W * S::NACC * (W * 32 * S::R) * 4 +
+           (size_t)(JS - 1) * S::R * S::NACC * 32 * 4 +
            (S::REC_SMEM ? (size_t)W * rec_bufs<S, W>() * S::REC_F4 * 32 * 16 : 0);
 }
 
-template <class S, int W>
+template <class S, int W, int JS = 1>
 cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
     constexpr int B = W * 32 * S::R;
-    constexpr size_t smem = sym_smem<S, W>();
-    auto k = sym_kernel<S, W, false>;
-    auto kt = sym_kernel<S, W, true>;
+    constexpr size_t smem = sym_smem<S, W, JS>();
+    auto k = sym_kernel<S, W, JS, false>;
+    auto kt = sym_kernel<S, W, JS, true>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
@@ -881,7 +918,7 @@ cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
         for (int s = 0; s < nt; ++s) {
             t.tile = s;
             const SymTile g = sym_tile(s, (int)nb, a.tile_w);
-            cudaError_t e = launch_ex((const void *)kt, dim3((unsigned)g.items()), dim3(W * 32), smem,
+            cudaError_t e = launch_ex((const void *)kt, dim3((unsigned)g.items()), dim3(sym_threads<W, JS>()), smem,
                                       s == 0 ? a.pdl != 0 : true, t, st);
             if (e != cudaSuccess) return e;
         }
@@ -889,7 +926,7 @@ cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
                          dim3(128), 0, true, t, st);
     }
     const unsigned items = (unsigned)(nb * (nb + 1) / 2);
-    cudaError_t e = launch_ex((const void *)k, dim3(items), dim3(W * 32), smem, a.pdl != 0, a, st);
+    cudaError_t e = launch_ex((const void *)k, dim3(items), dim3(sym_threads<W, JS>()), smem, a.pdl != 0, a, st);
     if (e != cudaSuccess) return e;
     // the epilogue is a programmatic dependent of the pair kernel: its launch
     // overlaps the pair kernel's last wave, and it waits for its completion
@@ -897,10 +934,11 @@ cudaError_t launch_sym(int, const ForceArgs &a, cudaStream_t st) {
                      dim3(32 * S::NACC), 0, true, a, st);
 }
 
-template <class S, int W>
+template <class S, int W, int JS = 1>
 int occ_sym(int) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel<S, W, false>, W * 32, sym_smem<S, W>()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel<S, W, JS, false>, sym_threads<W, JS>(),
+                                                      sym_smem<S, W, JS>()) !=
         cudaSuccess)
         return 0;
     return b;
@@ -909,11 +947,14 @@ int occ_sym(int) {
 // Shape (nt, r) = (threads per CTA, bodies per lane); the block is nt x r.
 const ForceEntry kAccel[] = {
     {32, SymAccel::R, &launch_sym<SymAccel, 1>, &occ_sym<SymAccel, 1>},   // blocks of 256
+    // blocks of 256, two warps splitting each block pair's j-chunks (64 threads x 4 bodies)
+    {64, SymAccel::R / 2, &launch_sym<SymAccel, 1, 2>, &occ_sym<SymAccel, 1, 2>},
     {64, SymAccel::R, &launch_sym<SymAccel, 2>, &occ_sym<SymAccel, 2>},   // blocks of 512
     {128, SymAccel::R, &launch_sym<SymAccel, 4>, &occ_sym<SymAccel, 4>},  // blocks of 1024
 };
 const ForceEntry kComp[] = {
     {32, SymComp::R, &launch_sym<SymComp, 1>, &occ_sym<SymComp, 1>},   // blocks of 256
+    {64, SymComp::R / 2, &launch_sym<SymComp, 1, 2>, &occ_sym<SymComp, 1, 2>},  // 256, j-chunks split
     {64, SymComp::R, &launch_sym<SymComp, 2>, &occ_sym<SymComp, 2>},   // blocks of 512
     {128, SymComp::R, &launch_sym<SymComp, 4>, &occ_sym<SymComp, 4>},  // blocks of 1024
 };

@@ -51,6 +51,36 @@ def test_sym_accel_matches_oracle(nbm, block, n):
         assert rel_l2(a, ref) <= 2e-5
 
 
+def test_sym_split_blocks_match_oracle(nbm):
+    """Blocks of 256 bodies whose block pairs two warps share, each taking
+    half of the j-chunks (the untuned choice from 16384 to 32767 bodies): a
+    ragged size (17000 bodies, 67 blocks) against the oracle in both
+    precisions and over a KDK run, bit-identical by tiles and on a repeat."""
+    n, G, eps, dt = 17000, 1.0, 0.01, 1e-3
+    s = ics.cube(n, seed=77)
+    ctx = nbm.Context(G, eps, dt)
+    if ctx.get_config(n)["tuned"]:
+        pytest.skip("a tuning table is loaded")
+    cfg = ctx.get_config(n)
+    assert (cfg["form"], cfg["threads"], cfg["bodies_per_thread"]) == ("pair_symmetric", 64, 4)
+    ref = oracle.accel(s.x, s.m, G, eps)
+    a = ctx.accel(_t(s.x), _t(s.m))
+    assert rel_l2(to_np(a), ref) <= 2e-5
+    assert torch.equal(ctx.accel(_t(s.x), _t(s.m)), a)
+    ctx.debug_set(nbm.NB_DBG_SYM_TILE, 5)
+    assert torch.equal(ctx.accel(_t(s.x), _t(s.m)), a)
+    comp = nbm.Context(G, eps, dt, precision="comp")
+    assert comp.get_config(n)["threads"] == 64
+    ac = comp.accel(_t(s.x, torch.float64), _t(s.m, torch.float64))
+    assert rel_l2(to_np(ac), ref) <= 1e-6
+    kdk = nbm.Context(G, eps, dt, scheme="kdk")
+    x, v = _t(s.x), _t(s.v)
+    kdk.run(x, v, _t(s.m), 3)
+    xr, vr = oracle.run(s.x, s.v, s.m, G, eps, dt, 3, scheme="kdk")
+    assert rel_l2(to_np(x), xr) <= 1e-5
+    assert rel_l2(to_np(v), vr) <= 1e-4
+
+
 def test_sym_accel_plummer_momentum(nbm):
     """Plummer sphere (the large-system workload's distribution): forces
     against the oracle, and the pair antisymmetry of the form itself: the
