@@ -352,7 +352,12 @@ typedef enum {
      * all), -1 =
      * one launch always, w > 0 = tiles of w blocks whenever that makes more
      * than one tile. Results are bit-identical either way. */
-    NB_DBG_SYM_TILE = 7
+    NB_DBG_SYM_TILE = 7,
+    /* nb_adjoint with a pair-symmetric VJP: 0 = each reverse step's
+     * preparation (v-bar update, the VJP's records) done by the previous
+     * step's VJP epilogue inside a checkpoint segment (default), 1 = by a
+     * kernel of its own every step. Results are bit-identical either way. */
+    NB_DBG_ADJ_PREP = 8
 } nb_debug_key;
 nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value);
 

@@ -271,6 +271,12 @@ nb_status nb_debug_set(nb_ctx *ctx, int key, int64_t value) {
         clear_graphs(ctx);
         return NB_OK;
     }
+    if (key == NB_DBG_ADJ_PREP) {
+        if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
+        ctx->adj_unfused = (int)value;
+        clear_graphs(ctx);
+        return NB_OK;
+    }
     if (key == NB_DBG_STALL_PRODUCER) {
         if (value != 0 && value != 1) return fail(ctx, NB_ERR_INVALID, "value must be 0 or 1");
         ctx->debug = value ? (ctx->debug | kDbgStallProducer) : (ctx->debug & ~kDbgStallProducer);

@@ -112,7 +112,8 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
     char key[512];
     snprintf(key, sizeof key, "adj|%lld|%p|%d|%p|%d|%p|%p|%p|%d.%d.%d.%d.%d|%d.%d.%d.%d.%d|%llu|%a|%a|%a",
              (long long)n, m, steps, ckpt, k, xbar0, vbar0, mbar, sf.pol, sf.nt, sf.r, sf.split,
-             sf.jt, sv.pol, sv.nt, sv.r, sv.split, sv.jt, (unsigned long long)ctx->timeout_ns * 4 + ctx->debug,
+             sf.jt, sv.pol, sv.nt, sv.r, sv.split, sv.jt,
+             (unsigned long long)ctx->timeout_ns * 8 + ctx->adj_unfused * 4 + ctx->debug,
              ctx->p.G, ctx->p.eps, ctx->p.dt);
     GraphEntry *g = graph_lookup(ctx, key);
     if (!g) {
@@ -164,25 +165,39 @@ nb_status nb_adjoint(nb_ctx *ctx, int64_t n, const void *m, int steps, const voi
                 if (rs == NB_OK) rs = fail(ctx, NB_ERR_CUDA, "adjoint capture: event");
         };
         // Sweep segment `seg` backwards on side.
+        // With a pair-symmetric VJP each step's epilogue (a kernel of its own,
+        // after every read of the records) also prepares the next step of
+        // the segment; the first step of a segment is prepared on its own.
+        const bool fuse = pol_is_sym(sv.pol) && !ctx->adj_unfused;
         auto sweep = [&](int seg) {
             const int b = seg & 1;
             if (!cuda_ok(cudaStreamWaitEvent(ctx->side, ev_rec[seg], 0))) return;
             const char *slot = (const char *)ckpt + (size_t)seg * slot_bytes;
+            auto x64_of = [&](int t) -> const double * {
+                return !f64 ? nullptr
+                            : t == 0 ? (const double *)slot
+                                     : (const double *)((char *)ctx->adj_traj64[b].p + (size_t)t * n * 48);
+            };
             for (int t = k - 1; rs == NB_OK && t >= 0; --t) {
-                const double *x64 = !f64 ? nullptr
-                                    : t == 0 ? (const double *)slot
-                                             : (const double *)((char *)ctx->adj_traj64[b].p + (size_t)t * n * 48);
-                if (!cuda_ok(launch_adj_prepare(n, npad, f64 ? 1 : 0, traj_slot(b, t), x64, 6, m, vbar0,
-                                                xbar0, ctx->p.dt, (float4 *)ctx->rec.p,
-                                                (double *)ctx->abar64.p, ctx->side)))
-                    return;
-                ctx->launches += 1;
+                if (!fuse || t == k - 1) {
+                    if (!cuda_ok(launch_adj_prepare(n, npad, f64 ? 1 : 0, traj_slot(b, t), x64_of(t), 6, m,
+                                                    vbar0, xbar0, ctx->p.dt, (float4 *)ctx->rec.p,
+                                                    (double *)ctx->abar64.p, ctx->side)))
+                        return;
+                    ctx->launches += 1;
+                }
                 ForceArgs a = base_args(ctx, pv, n, (const float4 *)ctx->rec.p);
                 a.op = kEpiVjp;
                 a.xbar = xbar0;
                 a.mbar = mbar;
                 a.abar64 = ctx->abar64.p;
                 a.mass = m;
+                if (fuse && t > 0) {
+                    a.prep_next = 1;
+                    a.next_xm = traj_slot(b, t - 1);
+                    a.next_x64 = x64_of(t - 1);
+                    a.vbar = vbar0;
+                }
                 rs = launch_force(ctx, pv, a, ctx->side);
             }
             if (rs == NB_OK && (!new_event(&ev_swp[seg]) || !cuda_ok(cudaEventRecord(ev_swp[seg], ctx->side))))

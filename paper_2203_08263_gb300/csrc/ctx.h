@@ -57,6 +57,7 @@ struct nb_ctx {
     int form_pin = 0;  // FP32 forward: 0 chosen per size, 1 one-sided only, 512/1024 pair-symmetric blocks
     int vjp_form_pin = 0;  // FP32 VJP: 0 chosen per size, 1 one-sided only, 256/512 pair-symmetric blocks
     int sym_tile = 0;      // pair-symmetric tiles: 0 chosen per size, -1 never, w > 0 tiles of w blocks
+    int adj_unfused = 0;   // nb_adjoint: 1 = every reverse step prepared by a kernel of its own
     std::map<int64_t, int> cluster_sizes;  // 2n + f64 -> cluster size of the one-cluster path (0: none)
     int64_t launches = 0;
     std::map<std::string, nb::detail::TuneEntry> tuned;

@@ -109,6 +109,15 @@ struct ForceArgs {
     int tile_w;
     int tile;
     int ntile;
+    // adjoint: the next reverse step's preparation fused into this VJP's
+    // epilogue (pair-symmetric VJPs only, whose epilogue is a kernel of its
+    // own that runs after every read of the records): vbar' = vbar + dt xbar
+    // with the xbar just updated, abar = dt/2 vbar', and each body's half of
+    // the next step's records from that step's positions
+    int prep_next;
+    const float4 *next_xm;   // FP32: the next step's packed positions
+    const double *next_x64;  // precision form: the next step's FP64 (x, v) rows [n][6]
+    void *vbar;              // [n][3] state-type, updated in place
 };
 
 // ---------------------------------------------------------------- helpers
@@ -921,6 +930,25 @@ struct VjpF32x2 {
 #pragma unroll
         for (int c = 0; c < 3; ++c) xb[c] += G * (mk * u[c] - f.v * ak[c] + 3.f * w[c]);
         reinterpret_cast<float *>(a.mbar)[k] += -G * f.p;
+        if (a.prep_next) {  // the next step's record half of body k (its mass stays)
+            float *vb = reinterpret_cast<float *>(a.vbar) + 3 * k;
+            const float dt = (float)a.dt;
+            float an[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float vn = vb[c] + dt * xb[c];  // vbar' = vbar + dt xbar
+                vb[c] = vn;
+                an[c] = dt / 2.0f * vn;               // abar = dt/2 vbar'
+            }
+            float *p = reinterpret_cast<float *>(const_cast<float4 *>(a.src) + (k >> 1) * 4);
+            const int h = (int)(k & 1);
+            p[0 + h] = pair_get(a.next_xm, k, 0);
+            p[2 + h] = pair_get(a.next_xm, k, 1);
+            p[4 + h] = pair_get(a.next_xm, k, 2);
+            p[8 + h] = an[0];
+            p[10 + h] = an[1];
+            p[12 + h] = an[2];
+        }
     }
 };
 
@@ -1045,6 +1073,35 @@ struct VjpComp {
 #pragma unroll
         for (int c = 0; c < 3; ++c) xb[c] += G * (mk * fs[c] - fs[3] * ak[c] + 3.0 * fs[4 + c]);
         reinterpret_cast<double *>(a.mbar)[k] += -G * fs[7];
+        if (a.prep_next) {  // the next step's record half of body k (its mass stays)
+            double *vb = reinterpret_cast<double *>(a.vbar) + 3 * k;
+            double *an = const_cast<double *>(ak);
+            const double dt = a.dt;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double vn = vb[c] + dt * xb[c];
+                vb[c] = vn;
+                an[c] = dt / 2.0 * vn;
+            }
+            float hi[3], lo[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double xc = a.next_x64[(int64_t)6 * k + c];
+                hi[c] = (float)xc;
+                lo[c] = (float)(xc - (double)hi[c]);
+            }
+            float *p = reinterpret_cast<float *>(const_cast<float4 *>(a.src) + (k >> 1) * 5);
+            const int h = (int)(k & 1);
+            p[0 + h] = hi[0];
+            p[2 + h] = hi[1];
+            p[4 + h] = hi[2];
+            p[8 + h] = (float)an[0];
+            p[10 + h] = (float)an[1];
+            p[12 + h] = (float)an[2];
+            p[14 + h] = lo[0];
+            p[16 + h] = lo[1];
+            p[18 + h] = lo[2];
+        }
     }
 };
 

@@ -21,7 +21,7 @@ NB_OK, NB_ERR_INVALID, NB_ERR_CUDA, NB_ERR_NOMEM, NB_ERR_TIMEOUT, NB_ERR_UNSUPPO
 NB_FP32, NB_FP32_COMP_FP64_STATE = 0, 1
 NB_SCHEME_PAPER, NB_SCHEME_KDK = 0, 1
 NB_DBG_WAIT_TIMEOUT_NS, NB_DBG_STALL_PRODUCER, NB_DBG_MATH_VARIANT, NB_DBG_RUN_PATH = 1, 2, 3, 4
-NB_DBG_FORM, NB_DBG_VJP_FORM, NB_DBG_SYM_TILE = 5, 6, 7
+NB_DBG_FORM, NB_DBG_VJP_FORM, NB_DBG_SYM_TILE, NB_DBG_ADJ_PREP = 5, 6, 7, 8
 MODE_FORWARD, MODE_ADJOINT, MODE_POTENTIAL = 0, 1, 2
 # nb_form values (nb_get_form)
 FORMS = {0: "f32x2", 1: "scalar", 2: "compensated", 3: "potential", 4: "vjp",

@@ -504,3 +504,37 @@ def test_sym_tiled_adjoint_bit_identical(nbm):
             grads[tile] = [t.clone() for t in g]
         for a, b in zip(grads[2], grads[-1]):
             assert torch.equal(a, b), prec
+
+
+def test_sym_adjoint_fused_preparation_bit_identical(nbm):
+    """nb_adjoint with each reverse step prepared by the previous step's VJP
+    epilogue (the default with a pair-symmetric VJP) gives the gradients of
+    a preparation kernel per step bit for bit, in both precisions, by tiles
+    and in one launch (the fused form's agreement with the FP64 oracle is
+    the other adjoint tests', which run it by default)."""
+    n, T, k = 3000, 12, 4
+    s = ics.cube(n, seed=24, masses="equal")
+    xstar = ics.targets(n, seed=24)
+    G, eps, dt = 1.0, 0.01, 1e-3
+    for prec, f in (("fp32", torch.float32), ("comp", torch.float64)):
+        for tile in (-1, 3):
+            grads = {}
+            for prep in (1, 0):
+                ctx = nbm.Context(G, eps, dt, precision=prec)
+                ctx.debug_set(nbm.NB_DBG_VJP_FORM, 256)
+                ctx.debug_set(nbm.NB_DBG_RUN_PATH, GRAPH)
+                ctx.debug_set(nbm.NB_DBG_SYM_TILE, tile)
+                ctx.debug_set(nbm.NB_DBG_ADJ_PREP, prep)
+                x, v, m = _t(s.x, f), _t(s.v, f), _t(s.m, f)
+                ck = torch.empty((T // k + 1, n, 6), dtype=f, device=DEV)
+                ctx.run(x, v, m, T, ckpt=ck, ckpt_every=k)
+                xbT = 2 * (x - _t(xstar, f))
+                before = ctx.launch_count
+                g = ctx.adjoint(m, T, ck, k, xbT, torch.zeros_like(xbT))
+                ctx.sync()
+                launches = ctx.launch_count - before
+                grads[prep] = ([t.clone() for t in g], launches)
+            for a, b in zip(grads[0][0], grads[1][0]):
+                assert torch.equal(a, b), (prec, tile)
+            # one preparation kernel per segment instead of one per step
+            assert grads[1][1] - grads[0][1] == T - T // k
