@@ -274,7 +274,11 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, int mode);
 
 /* The launch shape the context would use for (n, mode):
  * out[0..4] = {threads per CTA, bodies per thread, j-split, j-tile bodies,
- * 1 if the shape came from a tuning run}. */
+ * 1 if the shape came from a tuning run}. For the pair-symmetric forms the
+ * block is threads x bodies per thread (also reported as the j-tile); the
+ * forces' 256-body blocks come in two forms, 32 threads x 8 (one warp per
+ * block pair) and 64 x 4 (two warps sharing the block pair's bodies, each
+ * with half of its j-chunks; the untuned choice from 16384 to 32767 bodies). */
 nb_status nb_get_config(nb_ctx *ctx, int64_t n, int mode, int *out5);
 
 /* Force-sum forms (nb_get_form). */
@@ -337,9 +341,9 @@ typedef enum {
     NB_DBG_RUN_PATH = 4,
     /* Forward force form (FP32 and the precision form): 0 = chosen per size
      * (default), 1 = one-sided kernels only, 256, 512 or 1024 = the
-     * pair-symmetric kernel with blocks of that many bodies at every size
-     * (nb_run's graph path; the fused small-system paths keep their own
-     * kernel). */
+     * pair-symmetric kernel with blocks of that many bodies, one warp per
+     * 256 bodies of a block pair, at every size (nb_run's graph path; the
+     * fused small-system paths keep their own kernel). */
     NB_DBG_FORM = 5,
     /* VJP form (nb_vjp, nb_adjoint; FP32 and the precision form): 0 =
      * chosen per size (default), 1 = one-sided only, 256 or 512 = the
